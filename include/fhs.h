@@ -1,0 +1,203 @@
+/*
+ * fhs.h - C ABI of the GB300 (sm_103a) Faceted HyperSARA PDFB hot path.
+ *
+ * Method: Thouvenin, Abdulaziz, Dabbech, Repetti, Wiaux, "Parallel faceted
+ * imaging in radio interferometry via proximal splitting (Faceted HyperSARA)",
+ * arXiv 2003.07358.  One call of fhs_pdfb_iter performs iterations of
+ * Algorithm 2 on every spectral sub-cube ("cube") of a context.
+ *
+ * General conventions
+ *  - Every array argument is a DEVICE pointer owned by the caller unless the
+ *    comment says "host".  The library owns only its context (geometry tables,
+ *    sorted visibility coordinates, FFT and filter tables, scratch buffers).
+ *  - Real arrays are float32; complex arrays are complex64 stored as
+ *    interleaved (re, im) float pairs and passed as float*.
+ *  - Images are [L][n1][n2] row-major (channel, row, column).
+ *  - Visibility-domain arrays (y, v, u_prev, results of fhs_measure) are in the
+ *    context's INTERNAL order: channel-major, each channel sorted by grid
+ *    tile.  fhs_vis_to_internal / fhs_vis_to_user convert from / to the
+ *    caller's order (the order of the uv array given to fhs_create).
+ *  - All work is asynchronous on the stream given to fhs_create, except the
+ *    calls documented as synchronising.  Calls on one context must not overlap.
+ *  - Errors: every call returns an fhs_status; nothing aborts.  The message of
+ *    the last error is returned by fhs_last_error.  A CUDA error that leaves
+ *    the context unusable returns FHS_ERR_CUDA on every later call.
+ */
+#ifndef FHS_H
+#define FHS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fhs_ctx fhs_ctx;
+typedef int32_t fhs_status;
+
+enum {
+  FHS_OK = 0,
+  FHS_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+  FHS_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed   */
+  FHS_ERR_OOM = 3,         /* device memory for the context could not be allocated */
+  FHS_ERR_TIMEOUT = 4,     /* reserved: a bounded device-side wait gave up  */
+  FHS_ERR_NONFINITE = 5,   /* a norm reduction produced NaN or Inf          */
+  FHS_ERR_UNSUPPORTED = 6  /* shape outside what this build implements      */
+};
+
+enum { FHS_WIN_TRIANGULAR = 0, FHS_WIN_SINE = 1 };
+
+/* One spectral sub-cube (Section 2.4.1: channel-interleaved sub-problems
+ * are independent).  Shapes this build supports: n1, n2 powers of two in
+ * [16, 4096]; 1 <= L <= 64; 1 <= Qy <= n1/16, 1 <= Qx <= n2/16;
+ * 0 <= overlap < 0.5; 1 <= B <= 16.                                         */
+typedef struct {
+  int32_t n1, n2;        /* image rows, columns                                 */
+  int32_t L;             /* channels of this sub-cube                           */
+  int32_t Qy, Qx;        /* spatial facet grid, Section 2.4.2 (nuclear facets)  */
+  double overlap;        /* nuclear facet overlap, fraction of the tile side    */
+  int32_t window;        /* FHS_WIN_TRIANGULAR (Fig. 2) or FHS_WIN_SINE         */
+  int32_t B;             /* data blocks per channel, Eq. (2)                    */
+  const int64_t* M;      /* host [L*B]: visibilities of (channel l, block b)    */
+  const float* uv;       /* host [sum(M)][2]: (u, v) in rad/pixel, |u|,|v| < pi,
+                            channel-major, block-contiguous; u pairs with the
+                            column coordinate c - n2/2, v with the row r - n1/2 */
+  double tau, zeta, kappa;   /* step sizes of Algorithm 2 (Section 3.2)         */
+  const double* eta;     /* host [L]: eta_l = 1/||Phi_l||_S^2                   */
+  double mu;             /* mu_c = upsilon_c, Eq. (FHS sparsity heuristic)      */
+  const double* mu_bar;  /* host [Qy*Qx]: mu_bar_{c,q} = upsilon_bar_{c,q}      */
+  const double* eps;     /* host [L*B]: l2-ball radii eps_{l,b}, Eq. (3)        */
+} fhs_cube_desc;
+
+/* Sizes of the caller-owned arrays of one cube. */
+typedef struct {
+  int64_t n_pix;         /* n1*n2                                               */
+  int64_t n_vis;         /* total visibilities of the cube (all channels)       */
+  int64_t n_coef;        /* I: SARA coefficients per channel (layout below)     */
+  int64_t n_facet_pix;   /* sum over nuclear facets of their pixel count        */
+  int32_t n_facets;      /* Qy*Qx                                               */
+  int32_t n_blocks;      /* L*B                                                 */
+} fhs_sizes;
+
+/* Dual variables and weights of one cube (Algorithm 2 inputs), caller-owned:
+ *  W         [L][I] float: SARA dual, coefficient layout:
+ *            for basis b = db1..db8 (filter length 2b): for level j = 1..4:
+ *            subbands d0 (rows: low, cols: high), d1 (rows: high, cols: low),
+ *            d2 (high, high), each [r_j][c_j] row-major with
+ *            r_j = floor((r_{j-1} + 2b - 1)/2), r_0 = n1 (c_j likewise);
+ *            then LL4 [r_4][c_4]; after db8 the Dirac block [n1][n2].
+ *  theta     [I] float: l2,1 weights (Eq. 10), shared by the channels.
+ *  P         float: nuclear duals, facet q = qy*Qx + qx stored [L][h_q][w_q]
+ *            at offset L * sum_{q'<q} h_q' w_q'; facet q covers rows
+ *            [floor(qy n1/Qy) - o, floor((qy+1) n1/Qy)) with
+ *            o = floor(overlap * tile height) for qy > 0 (0 for qy = 0);
+ *            columns likewise.
+ *  theta_bar [Qy*Qx][L] float: nuclear weights (Eq. 9), index j pairs with the
+ *            j-th largest singular value.
+ *  v         [n_vis] complex64, internal order: data duals v_{l,b}.
+ *  u_prev    [n_vis] complex64, internal order: Phi x^{(p-1)} (Algorithm 2
+ *            extrapolation 2 Phi x^{(p)} - Phi x^{(p-1)}); set it to Phi x^{(0)}
+ *            (fhs_measure) before the first iteration.                       */
+typedef struct {
+  float* W;
+  float* theta;
+  float* P;
+  float* theta_bar;
+  float* v;
+  float* u_prev;
+} fhs_state;
+
+/* Per-cube arguments of fhs_pdfb_iter. */
+typedef struct {
+  float* X;              /* [L][n1][n2] primal iterate, updated in place        */
+  float* Xcheck;         /* [L][n1][n2] 2 X^{(p+1)} - X^{(p)}, updated in place */
+  const float* y;        /* [n_vis] complex64 data, internal order              */
+  fhs_state state;
+} fhs_iterate;
+
+/* Statistics of the last iteration of a cube (host). */
+typedef struct {
+  double xi;             /* ||X^{(p+1)} - X^{(p)}||_F / ||X^{(p)}||_F           */
+  double res_norm;       /* ||r||_2, r_{l,b} = ||y_{l,b} - Phi_{l,b} x_l^{(p)}|| */
+  double eps_norm;       /* ||eps||_2                                           */
+} fhs_iter_stats;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context for `ncubes` sub-cubes.  Sorts the visibilities of every
+ * channel by grid tile (host counting sort), builds the FFT, Kaiser-Bessel,
+ * Daubechies and facet tables and allocates scratch.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Synchronising.
+ * Errors: INVALID_ARG (shape, NULL pointer, non-finite parameter),
+ * UNSUPPORTED (shape outside this build), OOM, CUDA.                       */
+fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, fhs_ctx** out);
+fhs_status fhs_destroy(fhs_ctx* ctx);
+fhs_status fhs_get_sizes(const fhs_ctx* ctx, int32_t cube, fhs_sizes* out);
+/* Synchronise the context stream and report deferred errors. */
+fhs_status fhs_sync(fhs_ctx* ctx);
+/* Message of the last error of `ctx` (or of the last failed fhs_create when
+ * ctx is NULL); valid until the next call on the context. */
+const char* fhs_last_error(const fhs_ctx* ctx);
+
+/* Permutation of the cube's visibilities: perm[i] = caller index (0-based,
+ * within the cube's uv array) of internal visibility i.  Host [n_vis]. */
+fhs_status fhs_vis_permutation(const fhs_ctx* ctx, int32_t cube, int64_t* perm_host);
+/* internal[i] = user[perm[i]] and user[perm[i]] = internal[i] (complex64). */
+fhs_status fhs_vis_to_internal(fhs_ctx* ctx, int32_t cube, const float* user, float* internal);
+fhs_status fhs_vis_to_user(fhs_ctx* ctx, int32_t cube, const float* internal, float* user);
+
+/* -------------------------------------------------------------- operators */
+/* y = Phi x for every channel, Eq. (1): Phi_l = G_l F Z with Z the 2x
+ * zero-padding and Kaiser-Bessel deapodisation s = 1/phi_hat(2 pi p / K),
+ * F the 2n1 x 2n2 DFT (exp(-2 pi i k p / K), centred pixel coordinates), G
+ * the 7x7 Kaiser-Bessel interpolation (beta = 2.34 * 7, taps
+ * k_j = floor(t - 3.5) + 1 + j, t = omega K / 2 pi).
+ * x: [L][n1][n2] float; y: [n_vis] complex64, internal order (overwritten). */
+fhs_status fhs_measure(fhs_ctx* ctx, int32_t cube, const float* x, float* y);
+/* x = Re Phi^dagger v (exact transpose of fhs_measure, real part; Table 2
+ * last row restricts the primal to real images).  x overwritten. */
+fhs_status fhs_adjoint(fhs_ctx* ctx, int32_t cube, const float* v, float* x);
+/* ||Phi_l||_S^2 of every channel by the power method on Re(Phi^dagger Phi)
+ * (Section 2.3.1 footnote): stop at relative variation < rel_tol or after
+ * max_iter iterations; start vector all ones.  out: host [L].  Synchronising. */
+fhs_status fhs_opnorm_sq(fhs_ctx* ctx, int32_t cube, int32_t max_iter, double rel_tol, double* out);
+
+/* Psi^dagger x: SARA analysis of every channel (Section 2.3.1; layout of W).
+ * x [L][n1][n2] -> coef [L][I] (overwritten). */
+fhs_status fhs_sara_analysis(fhs_ctx* ctx, int32_t cube, const float* x, float* coef);
+/* Psi w: exact transpose of fhs_sara_analysis, coef [L][I] -> x [L][n1][n2] (overwritten). */
+fhs_status fhs_sara_synthesis(fhs_ctx* ctx, int32_t cube, const float* coef, float* x);
+
+/* ------------------------------------------------------ dual updates (Alg. 2) */
+/* Sparsity duals of every facet (Algorithm 2, W update and Table 2 row 3):
+ * W <- (I - prox_{kappa^-1 mu ||.||_{2,1,theta}})(W + Psi^dagger Xcheck),
+ * then A += kappa Psi W.  The faceted operators Psi_q^dagger S_q sum exactly
+ * to Psi^dagger (Section 2.4.2), so facets only partition W.  W in place. */
+fhs_status fhs_prox_l21_sara_facets(fhs_ctx* ctx, int32_t cube, const float* xcheck,
+                                    float* W, const float* theta, float* A);
+/* Low-rankness duals of every facet (Algorithm 2, P update, Table 2 row 2):
+ * P_q <- (I - prox_{zeta^-1 mu_bar_q ||.||_{*,theta_bar_q}})(P_q + D_q S~_q Xcheck),
+ * then A += zeta S~_q^T D_q P_q.  The prox is computed as P_q <- Z V diag(m) V^T
+ * with Z^T Z = V diag(s^2) V^T (FP64 eigen-solve) and m_j = min(1, alpha_j / s_j). */
+fhs_status fhs_prox_nuclear_facets(fhs_ctx* ctx, int32_t cube, const float* xcheck,
+                                   float* P, const float* theta_bar, float* A);
+/* Data duals with U = I (Table 2 row 4): for every (l, b),
+ * v_{l,b} = (z - y)(1 - min(1, eps_{l,b} / ||z - y||)) = (I - P_B(y, eps))(z).
+ * z, y, v_out: [n_vis] complex64 internal order; dnorm_out: host [L*B]
+ * receives ||z_{l,b} - y_{l,b}||_2 in FP64 (may be NULL).  Synchronising
+ * when dnorm_out is not NULL. */
+fhs_status fhs_proj_l2ball_blocks(fhs_ctx* ctx, int32_t cube, const float* z, const float* y,
+                                  float* v_out, double* dnorm_out);
+/* Weights of Algorithm 1 from x: theta_i = mu / (||[Psi^dagger x]_i||_2 + mu)
+ * (Eq. 10) and theta_bar_{q,j} = mu_bar_q / (s_j(D_q S~_q x) + mu_bar_q) (Eq. 9). */
+fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta, float* theta_bar);
+
+/* n_iter iterations of Algorithm 2 on every cube.  it: host [ncubes].
+ * stats: host [ncubes] or NULL; when not NULL the call synchronises and
+ * fills the statistics of the last iteration. */
+fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fhs_iter_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHS_H */

@@ -1,0 +1,151 @@
+// Internal declarations of the GB300 Faceted HyperSARA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fhs.h"
+
+namespace fhs {
+
+constexpr int kTaps = 7;          // Kaiser-Bessel support J
+constexpr int kPolyDeg = 11;      // per-tap polynomial degree of the kernel fit
+constexpr int kGridTile = 64;     // gridder tile side (cells)
+constexpr int kLevels = 4;        // SARA decomposition levels
+constexpr int kMaxB = 16;         // data blocks per channel
+constexpr int kMaxL = 64;         // channels per cube
+constexpr int kMaxFilt = 16;      // longest Daubechies filter (db8)
+
+// ------------------------------------------------------------ device tables
+// Kaiser-Bessel weights: phi(f + 2.5 - j) = sum_d kb_poly[j][d] (2f - 1)^d, f in [0, 1).
+struct KbPoly { float c[kTaps][kPolyDeg + 1]; };
+
+// Daubechies filters: h (low) and g (high) of db1..db8, filter b has length 2(b+1).
+struct Filters { float h[8][kMaxFilt]; float g[8][kMaxFilt]; };
+
+// ------------------------------------------------------------------- cube
+struct SaraLayout {
+  int rows[8][kLevels + 1], cols[8][kLevels + 1];
+  int64_t off[8][kLevels + 1][4];   // [basis][level 1..4][subband 0..2, 3 = LL4]
+  int64_t dirac_off;
+  int64_t I;
+};
+
+struct NucFacet {                    // one nuclear facet
+  int r0, r1, c0, c1;                // covered pixels [r0, r1) x [c0, c1)
+  int64_t p_off;                     // offset of its P block in units of floats (includes L)
+  int wy_off, wx_off;                // offsets of its 1-D windows in the window tables
+};
+
+struct Cube {
+  int n1, n2, L, Qy, Qx, B, window;
+  double rho, tau, zeta, kappa, mu;
+  std::vector<double> eta, mu_bar, eps;     // host copies
+  int K1, K2;
+  int N1c, N2c;                              // column FFT factorisation K1 = N1c * N2c
+  SaraLayout sara;
+  std::vector<NucFacet> facets;
+  int64_t n_facet_pix;
+  int max_facet_pix;
+  // visibilities
+  std::vector<int64_t> M_lb;                 // [L*B]
+  std::vector<int64_t> vis_off;              // [L+1] channel offsets (internal order == caller order per channel)
+  int64_t n_vis;
+  int64_t max_M;
+  std::vector<int64_t> perm_host;            // internal -> caller index
+  float2* d_uv = nullptr;                    // [n_vis] internal order
+  int64_t* d_vis_off = nullptr;              // [L+1]
+  uint8_t* d_blk = nullptr;                  // [n_vis] block id
+  int64_t* d_perm = nullptr;                 // [n_vis]
+  int32_t* d_tile_off = nullptr;             // [L][ntiles*4 + 1] per-channel tile/class offsets (relative)
+  int ntile_r, ntile_c, tile;                // gridder tiles
+  // device copies of per-cube parameters and tables
+  NucFacet* d_facets = nullptr;
+  float* d_win = nullptr;                    // window tables (y and x windows concatenated)
+  int* d_tile_of = nullptr;                  // [n1 + n2]: tile index of each row, then of each column
+  float* d_scale_r = nullptr;                // [n1] deapodisation s_r
+  float* d_scale_c = nullptr;                // [n2]
+  double* d_eps = nullptr;                   // [L*B]
+  float* d_eta = nullptr;                    // [L]
+  float* d_mubar = nullptr;                  // [Q]
+};
+
+struct Scratch {
+  float2* grid = nullptr;    size_t grid_elems = 0;     // [L][K1][K2]
+  float* coef = nullptr;     size_t coef_elems = 0;     // [L][I]
+  float* t0 = nullptr;       size_t t_elems = 0;        // SARA temporaries
+  float* t1 = nullptr;
+  float* t2 = nullptr;
+  float* t3 = nullptr;
+  float* img = nullptr;      size_t img_elems = 0;      // [L][n1][n2]
+  float* img2 = nullptr;
+  float2* vis = nullptr;     size_t vis_elems = 0;      // [n_vis]
+  double* red = nullptr;     size_t red_elems = 0;      // reduction partials
+  double* red_host = nullptr;                           // pinned host copy
+  float* gram = nullptr;     size_t gram_elems = 0;     // nuclear Gram partials
+  float* nucM = nullptr;     size_t nucM_elems = 0;     // [Q][L][L]
+  float* blk_scale = nullptr;                           // [L*B]
+  double* blk_out = nullptr;                            // [2][L*B]
+};
+
+}  // namespace fhs
+
+struct fhs_ctx {
+  cudaStream_t stream = nullptr;
+  std::vector<fhs::Cube> cubes;
+  fhs::Scratch s;
+  float2* d_tw = nullptr;          // twiddles exp(-2 pi i k / Kmax), k < Kmax
+  int Kmax = 0;
+  std::string err;
+  bool broken = false;
+};
+
+namespace fhs {
+
+// --------------------------------------------------------- kernel launchers
+// Tables (constant memory lives in the translation unit that uses it).
+cudaError_t upload_kb_poly(const KbPoly& p);
+cudaError_t upload_filters(const Filters& f);
+
+// FFT / NUFFT (nufft.cu)
+void launch_measure(fhs_ctx* ctx, const Cube& cb, const float* x, float2* y, cudaStream_t st);
+void launch_fft_forward(fhs_ctx* ctx, const Cube& cb, const float* x, float2* grid, cudaStream_t st);
+void launch_fft_adjoint(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta,
+                        bool accumulate, cudaStream_t st);
+void launch_degrid(const Cube& cb, const float2* grid, float2* out, cudaStream_t st);
+void launch_degrid_pdfb(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
+                        float2* u_prev, double* partials, int nparts, cudaStream_t st);
+int degrid_parts(const Cube& cb);
+void launch_block_finalize(const Cube& cb, const double* partials, int nparts, float* scale, double* out,
+                           cudaStream_t st);
+int host_first_tap(float om, int K);
+void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write,
+                 float2* grid, cudaStream_t st);
+void launch_l2ball_partials(const Cube& cb, const float2* z, const float2* y, float2* d,
+                            double* partials, int nparts, cudaStream_t st);
+void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, float2* v, cudaStream_t st);
+void launch_vis_gather(const int64_t* perm, int64_t n, const float2* in, float2* out, cudaStream_t st);
+void launch_vis_scatter(const int64_t* perm, int64_t n, const float2* in, float2* out, cudaStream_t st);
+
+// SARA (sara.cu)
+void launch_sara_analysis(fhs_ctx* ctx, const Cube& cb, const float* x, float* coef, cudaStream_t st);
+void launch_sara_synthesis(fhs_ctx* ctx, const Cube& cb, const float* coef, float* out, float scale,
+                           bool accumulate, cudaStream_t st);
+void launch_l21_dual(const Cube& cb, float* W, const float* coef, const float* theta, cudaStream_t st);
+void launch_l21_weights(const Cube& cb, const float* coef, float* theta, cudaStream_t st);
+
+// nuclear (nuclear.cu)
+void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P, const float* theta_bar,
+                    float* A, bool weights_mode, float* theta_bar_out, cudaStream_t st);
+
+// primal (primal.cu)
+void launch_primal(const Cube& cb, float* X, float* Xc, const float* A, double* partials, int nparts,
+                   cudaStream_t st);
+int primal_parts(const Cube& cb);
+void launch_sumsq(const float* a, int64_t n_per_ch, int L, double* partials, int nparts, cudaStream_t st);
+void launch_scale_by_channel(float* x, int64_t n_per_ch, int L, const double* inv, cudaStream_t st);
+
+}  // namespace fhs

@@ -1,0 +1,824 @@
+// Host side of the GB300 Faceted HyperSARA library: context set-up (tables,
+// facet geometry, visibility tile sort, scratch) and the C-ABI entry points
+// declared in include/fhs.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "fhs_internal.h"
+
+using namespace fhs;
+using cd = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+const double kPi = 3.14159265358979323846;
+
+// --------------------------------------------------------------- errors
+struct Fail {
+  fhs_status st;
+  std::string msg;
+};
+
+#define FHS_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? FHS_ERR_OOM : FHS_ERR_CUDA,            \
+                 std::string(#call) + ": " + cudaGetErrorString(e_)};                     \
+  } while (0)
+
+#define FHS_REQUIRE(cond, code, text)                  \
+  do {                                                 \
+    if (!(cond)) throw Fail{code, std::string(text)};  \
+  } while (0)
+
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Fail{FHS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+template <class F>
+fhs_status guarded(fhs_ctx* ctx, F&& f) {
+  if (!ctx) return FHS_ERR_INVALID_ARG;
+  if (ctx->broken) {
+    ctx->err = "context unusable after an earlier CUDA error: " + ctx->err;
+    return FHS_ERR_CUDA;
+  }
+  try {
+    f();
+    return FHS_OK;
+  } catch (const Fail& e) {
+    ctx->err = e.msg;
+    if (e.st == FHS_ERR_CUDA) ctx->broken = true;
+    return e.st;
+  } catch (const std::exception& e) {
+    ctx->err = e.what();
+    return FHS_ERR_CUDA;
+  }
+}
+
+// ------------------------------------------------- Daubechies filters
+// Roots of sum_k c[k] y^k by Durand-Kerner (Weierstrass) iterations, then
+// Newton polishing on the original polynomial.
+std::vector<cd> poly_roots(const std::vector<double>& c) {
+  const int n = (int)c.size() - 1;
+  std::vector<cd> a(n + 1);
+  for (int k = 0; k <= n; ++k) a[k] = c[k] / c[n];
+  auto eval = [&](cd z) {
+    cd p = a[n];
+    for (int k = n - 1; k >= 0; --k) p = p * z + a[k];
+    return p;
+  };
+  std::vector<cd> z(n);
+  cd seed(0.4, 0.9);
+  for (int k = 0; k < n; ++k) z[k] = std::pow(seed, k + 1);
+  for (int it = 0; it < 2000; ++it) {
+    double change = 0.0;
+    for (int k = 0; k < n; ++k) {
+      cd den = 1.0;
+      for (int j = 0; j < n; ++j)
+        if (j != k) den *= (z[k] - z[j]);
+      cd dz = eval(z[k]) / den;
+      z[k] -= dz;
+      change = std::max(change, std::abs(dz) / (1.0 + std::abs(z[k])));
+    }
+    if (change < 1e-16) break;
+  }
+  for (int k = 0; k < n; ++k) {
+    for (int it = 0; it < 5; ++it) {
+      cd p = a[n], dp = 0.0;
+      for (int j = n - 1; j >= 0; --j) {
+        dp = dp * z[k] + p;
+        p = p * z[k] + a[j];
+      }
+      if (std::abs(dp) == 0.0) break;
+      z[k] -= p / dp;
+    }
+  }
+  return z;
+}
+
+// Extremal-phase Daubechies scaling filter of order N (length 2N):
+// |H|^2 = 2 cos^{2N}(w/2) P_N(sin^2(w/2)), P_N(y) = sum_{k<N} C(N-1+k, k) y^k;
+// each root y_i of P_N contributes the root z_i of z + 1/z = 2 - 4 y_i inside
+// the unit circle; H(w) = c (1 + w)^N prod (1 - z_i w), sum h = sqrt(2).
+std::vector<double> daubechies(int N) {
+  std::vector<cd> poly{cd(1.0)};
+  auto mul = [&](cd a0, cd a1) {   // poly *= (a0 + a1 w)
+    std::vector<cd> out(poly.size() + 1, cd(0.0));
+    for (size_t k = 0; k < poly.size(); ++k) {
+      out[k] += poly[k] * a0;
+      out[k + 1] += poly[k] * a1;
+    }
+    poly.swap(out);
+  };
+  if (N > 1) {
+    std::vector<double> p(N);
+    for (int k = 0; k < N; ++k) {
+      double binom = 1.0;   // C(N-1+k, k)
+      for (int i = 1; i <= k; ++i) binom = binom * (N - 1 + i) / i;
+      p[k] = binom;
+    }
+    for (cd y : poly_roots(p)) {
+      cd b = 2.0 - 4.0 * y;
+      cd disc = std::sqrt(b * b - 4.0);
+      cd z1 = (b + disc) / 2.0, z2 = (b - disc) / 2.0;
+      cd z = std::abs(z1) < 1.0 ? z1 : z2;
+      mul(cd(1.0), -z);
+    }
+  }
+  for (int k = 0; k < N; ++k) mul(cd(1.0), cd(1.0));
+  std::vector<double> h(poly.size());
+  double s = 0.0;
+  for (size_t k = 0; k < poly.size(); ++k) {
+    h[k] = poly[k].real();
+    s += h[k];
+  }
+  for (double& v : h) v *= sqrt(2.0) / s;
+  double e = 0.0;
+  for (double v : h) e += v * v;
+  FHS_REQUIRE(fabs(e - 1.0) < 1e-10, FHS_ERR_CUDA, "Daubechies construction lost orthonormality");
+  return h;
+}
+
+// ----------------------------------------------------- Kaiser-Bessel
+const double kBeta = 2.34 * 7.0;
+
+double bessel_i0(double x) {   // power series sum (x^2/4)^k / (k!)^2
+  double q = x * x / 4.0, t = 1.0, s = 1.0;
+  for (int k = 1; k < 500; ++k) {
+    t *= q / ((double)k * k);
+    s += t;
+    if (t < 1e-18 * s) break;
+  }
+  return s;
+}
+
+double kb_phi(double u) {
+  double a = 1.0 - (2.0 * u / 7.0) * (2.0 * u / 7.0);
+  if (a < 0.0) return 0.0;
+  return bessel_i0(kBeta * sqrt(a)) / bessel_i0(kBeta);
+}
+
+// Continuous Fourier transform of phi: 7 sinh(z) / z / I0(beta), z = sqrt(beta^2 - (7 theta / 2)^2).
+double kb_phi_hat(double theta) {
+  double r = kBeta * kBeta - (3.5 * theta) * (3.5 * theta);
+  double v;
+  if (r > 0) { double z = sqrt(r); v = sinh(z) / z; }
+  else if (r < 0) { double z = sqrt(-r); v = sin(z) / z; }
+  else v = 1.0;
+  return 7.0 * v / bessel_i0(kBeta);
+}
+
+// Chebyshev interpolation of phi(f + 2.5 - j), f = (x + 1)/2, x in [-1, 1], as
+// monomials in x; the fit error is checked against phi in double.
+KbPoly kb_poly() {
+  const int D = kPolyDeg;
+  KbPoly out;
+  double worst = 0.0;
+  for (int j = 0; j < kTaps; ++j) {
+    std::vector<double> xs(D + 1), fs(D + 1);
+    for (int k = 0; k <= D; ++k) {
+      xs[k] = cos(kPi * (k + 0.5) / (D + 1));
+      fs[k] = kb_phi((xs[k] + 1.0) / 2.0 + 2.5 - j);
+    }
+    std::vector<double> cheb(D + 1, 0.0);
+    for (int m = 0; m <= D; ++m) {
+      double s = 0.0;
+      for (int k = 0; k <= D; ++k) s += fs[k] * cos(m * kPi * (k + 0.5) / (D + 1));
+      cheb[m] = s * 2.0 / (D + 1);
+    }
+    cheb[0] *= 0.5;
+    // Chebyshev -> monomial: T_0 = 1, T_1 = x, T_{m+1} = 2x T_m - T_{m-1}
+    std::vector<double> mono(D + 1, 0.0), tm1(D + 1, 0.0), tm(D + 1, 0.0), tp(D + 1, 0.0);
+    tm1[0] = 1.0;
+    tm[1] = 1.0;
+    mono[0] += cheb[0];
+    for (int d = 0; d <= D; ++d) mono[d] += cheb[1] * tm[d];
+    for (int m = 2; m <= D; ++m) {
+      std::fill(tp.begin(), tp.end(), 0.0);
+      for (int d = 0; d < D; ++d) tp[d + 1] += 2.0 * tm[d];
+      for (int d = 0; d <= D; ++d) tp[d] -= tm1[d];
+      for (int d = 0; d <= D; ++d) mono[d] += cheb[m] * tp[d];
+      tm1 = tm;
+      tm = tp;
+    }
+    for (int d = 0; d <= D; ++d) out.c[j][d] = (float)mono[d];
+    for (int t = 0; t <= 200; ++t) {
+      double x = -1.0 + 2.0 * t / 200.0, p = 0.0;
+      for (int d = D; d >= 0; --d) p = p * x + mono[d];
+      worst = std::max(worst, fabs(p - kb_phi((x + 1.0) / 2.0 + 2.5 - j)));
+    }
+  }
+  FHS_REQUIRE(worst < 1e-8, FHS_ERR_CUDA, "Kaiser-Bessel polynomial fit is inaccurate");
+  return out;
+}
+
+// ------------------------------------------------------------ geometry
+std::vector<int> tile_bounds(int n, int Q) {
+  std::vector<int> b(Q + 1);
+  for (int i = 0; i <= Q; ++i) b[i] = (int)(((int64_t)i * n) / Q);
+  return b;
+}
+
+double window_w(int i, int o, int kind) {
+  if (kind == FHS_WIN_TRIANGULAR) return (i + 1.0) / (o + 1.0);
+  double s = sin(kPi * (i + 1.0) / (2.0 * (o + 1.0)));
+  return s * s;
+}
+
+// 1-D nuclear facets along one axis: start, end and window per tile.
+void nuclear_axis(int n, int Q, double rho, int kind, std::vector<int>& start, std::vector<int>& end,
+                  std::vector<std::vector<float>>& win) {
+  std::vector<int> tb = tile_bounds(n, Q);
+  std::vector<int> ov(Q);
+  for (int i = 0; i < Q; ++i) ov[i] = i == 0 ? 0 : (int)floor(rho * (tb[i + 1] - tb[i]));
+  start.resize(Q);
+  end.resize(Q);
+  win.resize(Q);
+  for (int i = 0; i < Q; ++i) {
+    start[i] = tb[i] - ov[i];
+    end[i] = tb[i + 1];
+    std::vector<double> w(end[i] - start[i], 1.0);
+    for (int k = 0; k < ov[i]; ++k) w[k] = window_w(k, ov[i], kind);
+    if (i + 1 < Q && ov[i + 1] > 0) {
+      int o2 = ov[i + 1];
+      for (int k = 0; k < o2; ++k) w[(end[i] - o2 - start[i]) + k] = 1.0 - window_w(k, o2, kind);
+    }
+    win[i].assign(w.begin(), w.end());
+  }
+}
+
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+template <class T>
+T* dalloc(size_t n) {
+  T* p = nullptr;
+  if (n == 0) n = 1;
+  FHS_CUDA(cudaMalloc((void**)&p, n * sizeof(T)));
+  return p;
+}
+
+template <class T>
+void upload(T* dst, const T* src, size_t n, cudaStream_t st) {
+  if (n) FHS_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
+  FHS_REQUIRE(d.M && d.uv && d.eta && d.mu_bar && d.eps, FHS_ERR_INVALID_ARG, "NULL host array in cube descriptor");
+  FHS_REQUIRE(pow2(d.n1) && pow2(d.n2) && d.n1 >= 16 && d.n2 >= 16, FHS_ERR_UNSUPPORTED,
+              "n1, n2 must be powers of two >= 16");
+  FHS_REQUIRE(d.n1 <= 4096 && d.n2 <= 4096, FHS_ERR_UNSUPPORTED, "n1, n2 must be <= 4096");
+  FHS_REQUIRE(d.L >= 1 && d.L <= kMaxL, FHS_ERR_UNSUPPORTED, "L must be in [1, 64]");
+  FHS_REQUIRE(d.Qy >= 1 && d.Qx >= 1 && d.Qy <= d.n1 / 16 + (d.n1 < 16) && d.Qx <= d.n2 / 16 + (d.n2 < 16),
+              FHS_ERR_UNSUPPORTED, "facet grid must satisfy 1 <= Q <= n/16");
+  FHS_REQUIRE(d.overlap >= 0.0 && d.overlap < 0.5, FHS_ERR_INVALID_ARG, "overlap must be in [0, 0.5)");
+  FHS_REQUIRE(d.window == FHS_WIN_TRIANGULAR || d.window == FHS_WIN_SINE, FHS_ERR_INVALID_ARG, "unknown window");
+  FHS_REQUIRE(d.B >= 1 && d.B <= kMaxB, FHS_ERR_UNSUPPORTED, "B must be in [1, 16]");
+  FHS_REQUIRE(std::isfinite(d.tau) && std::isfinite(d.zeta) && std::isfinite(d.kappa) && std::isfinite(d.mu) &&
+                  d.tau > 0 && d.zeta > 0 && d.kappa > 0 && d.mu >= 0,
+              FHS_ERR_INVALID_ARG, "tau, zeta, kappa must be positive and mu non-negative");
+  cb.n1 = d.n1; cb.n2 = d.n2; cb.L = d.L; cb.Qy = d.Qy; cb.Qx = d.Qx; cb.B = d.B; cb.window = d.window;
+  cb.rho = d.overlap; cb.tau = d.tau; cb.zeta = d.zeta; cb.kappa = d.kappa; cb.mu = d.mu;
+  cb.eta.assign(d.eta, d.eta + d.L);
+  cb.mu_bar.assign(d.mu_bar, d.mu_bar + d.Qy * d.Qx);
+  cb.eps.assign(d.eps, d.eps + d.L * d.B);
+  for (double v : cb.eta) FHS_REQUIRE(std::isfinite(v) && v > 0, FHS_ERR_INVALID_ARG, "eta must be positive");
+  for (double v : cb.mu_bar) FHS_REQUIRE(std::isfinite(v) && v >= 0, FHS_ERR_INVALID_ARG, "mu_bar must be >= 0");
+  for (double v : cb.eps) FHS_REQUIRE(std::isfinite(v) && v >= 0, FHS_ERR_INVALID_ARG, "eps must be >= 0");
+  cb.K1 = 2 * d.n1;
+  cb.K2 = 2 * d.n2;
+  if (cb.K1 <= 1024) { cb.N1c = cb.K1; cb.N2c = 1; }
+  else { cb.N1c = 64; cb.N2c = cb.K1 / 64; }
+
+  // SARA layout
+  SaraLayout& S = cb.sara;
+  int64_t cur = 0;
+  for (int b = 0; b < 8; ++b) {
+    int F = 2 * (b + 1);
+    S.rows[b][0] = d.n1;
+    S.cols[b][0] = d.n2;
+    for (int j = 1; j <= kLevels; ++j) {
+      S.rows[b][j] = (S.rows[b][j - 1] + F - 1) / 2;
+      S.cols[b][j] = (S.cols[b][j - 1] + F - 1) / 2;
+    }
+    for (int j = 1; j <= kLevels; ++j) {
+      int64_t sz = (int64_t)S.rows[b][j] * S.cols[b][j];
+      for (int s = 0; s < 3; ++s) { S.off[b][j][s] = cur; cur += sz; }
+    }
+    S.off[b][kLevels][3] = cur;
+    cur += (int64_t)S.rows[b][kLevels] * S.cols[b][kLevels];
+  }
+  S.dirac_off = cur;
+  cur += (int64_t)d.n1 * d.n2;
+  S.I = cur;
+
+  // nuclear facets
+  std::vector<int> ys, ye, xs, xe;
+  std::vector<std::vector<float>> wy, wx;
+  nuclear_axis(d.n1, d.Qy, d.overlap, d.window, ys, ye, wy);
+  nuclear_axis(d.n2, d.Qx, d.overlap, d.window, xs, xe, wx);
+  std::vector<float> win;
+  std::vector<int> wy_off(d.Qy), wx_off(d.Qx);
+  for (int i = 0; i < d.Qy; ++i) { wy_off[i] = (int)win.size(); win.insert(win.end(), wy[i].begin(), wy[i].end()); }
+  for (int i = 0; i < d.Qx; ++i) { wx_off[i] = (int)win.size(); win.insert(win.end(), wx[i].begin(), wx[i].end()); }
+  cb.facets.clear();
+  int64_t poff = 0;
+  cb.max_facet_pix = 0;
+  for (int qy = 0; qy < d.Qy; ++qy)
+    for (int qx = 0; qx < d.Qx; ++qx) {
+      NucFacet f;
+      f.r0 = ys[qy]; f.r1 = ye[qy]; f.c0 = xs[qx]; f.c1 = xe[qx];
+      f.p_off = poff;
+      f.wy_off = wy_off[qy];
+      f.wx_off = wx_off[qx];
+      int np = (f.r1 - f.r0) * (f.c1 - f.c0);
+      FHS_REQUIRE(np >= d.L, FHS_ERR_UNSUPPORTED, "a nuclear facet has fewer pixels than channels");
+      cb.max_facet_pix = std::max(cb.max_facet_pix, np);
+      poff += (int64_t)np * d.L;
+      cb.facets.push_back(f);
+    }
+  cb.n_facet_pix = poff / d.L;
+  std::vector<int> tile_of(d.n1 + d.n2);
+  {
+    std::vector<int> tb = tile_bounds(d.n1, d.Qy);
+    for (int r = 0, t = 0; r < d.n1; ++r) { while (r >= tb[t + 1]) ++t; tile_of[r] = t; }
+    std::vector<int> tc = tile_bounds(d.n2, d.Qx);
+    for (int c = 0, t = 0; c < d.n2; ++c) { while (c >= tc[t + 1]) ++t; tile_of[d.n1 + c] = t; }
+  }
+
+  // deapodisation s = 1 / phi_hat(2 pi p / K), p = i - n/2
+  std::vector<float> sr(d.n1), sc(d.n2);
+  for (int i = 0; i < d.n1; ++i) sr[i] = (float)(1.0 / kb_phi_hat(2.0 * kPi * (i - d.n1 / 2) / cb.K1));
+  for (int i = 0; i < d.n2; ++i) sc[i] = (float)(1.0 / kb_phi_hat(2.0 * kPi * (i - d.n2 / 2) / cb.K2));
+
+  // visibilities: per-channel tile sort (counting sort, stable)
+  cb.M_lb.assign(d.M, d.M + d.L * d.B);
+  cb.vis_off.assign(d.L + 1, 0);
+  cb.max_M = 0;
+  for (int l = 0; l < d.L; ++l) {
+    int64_t m = 0;
+    for (int b = 0; b < d.B; ++b) {
+      FHS_REQUIRE(cb.M_lb[l * d.B + b] >= 0, FHS_ERR_INVALID_ARG, "negative visibility count");
+      m += cb.M_lb[l * d.B + b];
+    }
+    FHS_REQUIRE(m < (int64_t)1 << 31, FHS_ERR_UNSUPPORTED, "more than 2^31 visibilities in a channel");
+    cb.vis_off[l + 1] = cb.vis_off[l] + m;
+    cb.max_M = std::max(cb.max_M, m);
+  }
+  cb.n_vis = cb.vis_off[d.L];
+  cb.tile = std::min(kGridTile, std::min(cb.K1, cb.K2));
+  cb.ntile_r = cb.K1 / cb.tile;
+  cb.ntile_c = cb.K2 / cb.tile;
+  const int T = cb.tile;
+  const int nkeys = cb.ntile_r * cb.ntile_c * 4;
+  cb.perm_host.assign(cb.n_vis, 0);
+  std::vector<int32_t> tile_off((size_t)d.L * (nkeys + 1));
+  std::vector<float2> uv_int(cb.n_vis);
+  std::vector<uint8_t> blk_int(cb.n_vis);
+  std::vector<int32_t> key, cnt(nkeys + 1);
+  std::vector<uint8_t> blk_user;
+  for (int l = 0; l < d.L; ++l) {
+    const int64_t off = cb.vis_off[l], m = cb.vis_off[l + 1] - off;
+    key.assign(m, 0);
+    blk_user.assign(m, 0);
+    {
+      int64_t k = 0;
+      for (int b = 0; b < d.B; ++b)
+        for (int64_t t = 0; t < cb.M_lb[l * d.B + b]; ++t) blk_user[k++] = (uint8_t)b;
+    }
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int64_t i = 0; i < m; ++i) {
+      float u = d.uv[2 * (off + i)], v = d.uv[2 * (off + i) + 1];
+      FHS_REQUIRE(std::isfinite(u) && std::isfinite(v) && fabsf(u) < (float)kPi && fabsf(v) < (float)kPi,
+                  FHS_ERR_INVALID_ARG, "uv coordinates must be finite and inside (-pi, pi)");
+      int kr = host_first_tap(v, cb.K1) & (cb.K1 - 1);
+      int kc = host_first_tap(u, cb.K2) & (cb.K2 - 1);
+      int tr = kr / T, tc = kc / T, lr = kr % T, lc = kc % T;
+      bool down = lr + kTaps - 1 >= T, right = lc + kTaps - 1 >= T;
+      int cls = down ? (right ? 2 : 1) : (right ? 3 : 0);
+      key[i] = (tr * cb.ntile_c + tc) * 4 + cls;
+      cnt[key[i] + 1]++;
+    }
+    for (int k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
+    int32_t* to = &tile_off[(size_t)l * (nkeys + 1)];
+    for (int k = 0; k <= nkeys; ++k) to[k] = cnt[k];
+    for (int64_t i = 0; i < m; ++i) {
+      int64_t pos = off + cnt[key[i]]++;
+      cb.perm_host[pos] = off + i;
+      uv_int[pos] = make_float2(d.uv[2 * (off + i)], d.uv[2 * (off + i) + 1]);
+      blk_int[pos] = blk_user[i];
+    }
+  }
+
+  // device copies
+  cb.d_uv = dalloc<float2>(cb.n_vis);
+  cb.d_blk = dalloc<uint8_t>(cb.n_vis);
+  cb.d_perm = dalloc<int64_t>(cb.n_vis);
+  cb.d_vis_off = dalloc<int64_t>(d.L + 1);
+  cb.d_tile_off = dalloc<int32_t>(tile_off.size());
+  cb.d_facets = dalloc<NucFacet>(cb.facets.size());
+  cb.d_win = dalloc<float>(win.size());
+  cb.d_tile_of = dalloc<int>(tile_of.size());
+  cb.d_scale_r = dalloc<float>(d.n1);
+  cb.d_scale_c = dalloc<float>(d.n2);
+  cb.d_eps = dalloc<double>(cb.eps.size());
+  cb.d_eta = dalloc<float>(d.L);
+  cb.d_mubar = dalloc<float>(cb.mu_bar.size());
+  std::vector<float> eta_f(cb.eta.begin(), cb.eta.end()), mub_f(cb.mu_bar.begin(), cb.mu_bar.end());
+  upload(cb.d_uv, uv_int.data(), uv_int.size(), st);
+  upload(cb.d_blk, blk_int.data(), blk_int.size(), st);
+  upload(cb.d_perm, cb.perm_host.data(), cb.perm_host.size(), st);
+  upload(cb.d_vis_off, cb.vis_off.data(), cb.vis_off.size(), st);
+  upload(cb.d_tile_off, tile_off.data(), tile_off.size(), st);
+  upload(cb.d_facets, cb.facets.data(), cb.facets.size(), st);
+  upload(cb.d_win, win.data(), win.size(), st);
+  upload(cb.d_tile_of, tile_of.data(), tile_of.size(), st);
+  upload(cb.d_scale_r, sr.data(), sr.size(), st);
+  upload(cb.d_scale_c, sc.data(), sc.size(), st);
+  upload(cb.d_eps, cb.eps.data(), cb.eps.size(), st);
+  upload(cb.d_eta, eta_f.data(), eta_f.size(), st);
+  upload(cb.d_mubar, mub_f.data(), mub_f.size(), st);
+  FHS_CUDA(cudaStreamSynchronize(st));
+}
+
+void free_cube(Cube& cb) {
+  void* ps[] = {cb.d_uv, cb.d_blk, cb.d_perm, cb.d_vis_off, cb.d_tile_off, cb.d_facets, cb.d_win, cb.d_tile_of,
+                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+}
+
+void alloc_scratch(fhs_ctx* ctx) {
+  Scratch& s = ctx->s;
+  size_t grid = 0, coef = 0, tlx = 0, tll = 0, img = 0, vis = 0, red = 2 * 1216 + 16, gram = 0, nm = 0, lb = 0;
+  for (const Cube& cb : ctx->cubes) {
+    const size_t L = cb.L;
+    grid = std::max(grid, L * cb.K1 * cb.K2);
+    coef = std::max(coef, L * (size_t)cb.sara.I);
+    for (int b = 0; b < 8; ++b)
+      for (int j = 1; j <= kLevels; ++j) {
+        tlx = std::max(tlx, L * cb.sara.rows[b][j - 1] * cb.sara.cols[b][j]);
+        tll = std::max(tll, L * cb.sara.rows[b][j] * cb.sara.cols[b][j]);
+      }
+    img = std::max(img, L * cb.n1 * cb.n2);
+    vis = std::max(vis, (size_t)cb.n_vis);
+    red = std::max(red, L * (size_t)degrid_parts(cb) * 2 * cb.B);
+    red = std::max(red, L * 64 * 2);
+    int nch = (cb.max_facet_pix + 1023) / 1024;
+    gram = std::max(gram, (size_t)cb.facets.size() * nch * L * L);
+    nm = std::max(nm, (size_t)cb.facets.size() * L * L);
+    lb = std::max(lb, L * cb.B);
+  }
+  s.grid = dalloc<float2>(grid); s.grid_elems = grid;
+  s.coef = dalloc<float>(coef); s.coef_elems = coef;
+  s.t0 = dalloc<float>(tlx); s.t1 = dalloc<float>(tlx);
+  s.t2 = dalloc<float>(tll); s.t3 = dalloc<float>(tll);
+  s.t_elems = tlx;
+  s.img = dalloc<float>(img); s.img2 = dalloc<float>(img); s.img_elems = img;
+  s.vis = dalloc<float2>(vis); s.vis_elems = vis;
+  s.red = dalloc<double>(red); s.red_elems = red;
+  FHS_CUDA(cudaMallocHost((void**)&s.red_host, red * sizeof(double)));
+  s.gram = dalloc<float>(gram); s.gram_elems = gram;
+  s.nucM = dalloc<float>(nm); s.nucM_elems = nm;
+  s.blk_scale = dalloc<float>(lb);
+  s.blk_out = dalloc<double>(2 * lb + 2 * kMaxL);
+}
+
+void free_scratch(Scratch& s) {
+  void* ps[] = {s.grid, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.img2, s.vis, s.red, s.gram, s.nucM, s.blk_scale,
+                s.blk_out};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  if (s.red_host) cudaFreeHost(s.red_host);
+}
+
+const Cube& get_cube(fhs_ctx* ctx, int32_t c) {
+  FHS_REQUIRE(c >= 0 && c < (int32_t)ctx->cubes.size(), FHS_ERR_INVALID_ARG, "cube index out of range");
+  return ctx->cubes[c];
+}
+
+// ------------------------------------------------------ composite steps
+void sara_dual(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* W, const float* theta, float* A) {
+  cudaStream_t st = ctx->stream;
+  launch_sara_analysis(ctx, cb, xcheck, ctx->s.coef, st);
+  launch_l21_dual(cb, W, ctx->s.coef, theta, st);
+  launch_sara_synthesis(ctx, cb, W, A, (float)cb.kappa, true, st);
+  check_launch("sara dual");
+}
+
+void adjoint_into(fhs_ctx* ctx, const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write,
+                  float* out, const float* eta, bool accumulate) {
+  cudaStream_t st = ctx->stream;
+  launch_grid(cb, vals, blk_scale, v_write, ctx->s.grid, st);
+  launch_fft_adjoint(ctx, cb, ctx->s.grid, out, eta, accumulate, st);
+  check_launch("adjoint");
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, fhs_ctx** out) {
+  if (!out) { g_create_err = "out is NULL"; return FHS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!cubes || ncubes < 1) { g_create_err = "need at least one cube"; return FHS_ERR_INVALID_ARG; }
+  fhs_ctx* ctx = new fhs_ctx();
+  ctx->stream = (cudaStream_t)stream;
+  try {
+    upload_kb_poly(kb_poly());
+    Filters filt;
+    memset(&filt, 0, sizeof(filt));
+    for (int b = 0; b < 8; ++b) {
+      std::vector<double> h = daubechies(b + 1);
+      int F = (int)h.size();
+      for (int k = 0; k < F; ++k) {
+        filt.h[b][k] = (float)h[k];
+        filt.g[b][k] = (float)((k % 2 ? -1.0 : 1.0) * h[F - 1 - k]);
+      }
+    }
+    FHS_CUDA(upload_filters(filt));
+    ctx->cubes.resize(ncubes);
+    for (int c = 0; c < ncubes; ++c) build_cube(ctx->cubes[c], cubes[c], ctx->stream);
+    int kmax = 0;
+    for (const Cube& cb : ctx->cubes) kmax = std::max(kmax, std::max(cb.K1, cb.K2));
+    ctx->Kmax = kmax;
+    std::vector<float2> tw(kmax);
+    for (int k = 0; k < kmax; ++k) {
+      double a = -2.0 * kPi * k / kmax;
+      tw[k] = make_float2((float)cos(a), (float)sin(a));
+    }
+    ctx->d_tw = dalloc<float2>(kmax);
+    upload(ctx->d_tw, tw.data(), tw.size(), ctx->stream);
+    alloc_scratch(ctx);
+    FHS_CUDA(cudaStreamSynchronize(ctx->stream));
+  } catch (const Fail& e) {
+    g_create_err = e.msg;
+    for (Cube& cb : ctx->cubes) free_cube(cb);
+    free_scratch(ctx->s);
+    if (ctx->d_tw) cudaFree(ctx->d_tw);
+    delete ctx;
+    return e.st;
+  }
+  *out = ctx;
+  return FHS_OK;
+}
+
+fhs_status fhs_destroy(fhs_ctx* ctx) {
+  if (!ctx) return FHS_ERR_INVALID_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  for (Cube& cb : ctx->cubes) free_cube(cb);
+  free_scratch(ctx->s);
+  if (ctx->d_tw) cudaFree(ctx->d_tw);
+  delete ctx;
+  return FHS_OK;
+}
+
+fhs_status fhs_get_sizes(const fhs_ctx* cctx, int32_t cube, fhs_sizes* out) {
+  fhs_ctx* ctx = const_cast<fhs_ctx*>(cctx);
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(out, FHS_ERR_INVALID_ARG, "out is NULL");
+    const Cube& cb = get_cube(ctx, cube);
+    out->n_pix = (int64_t)cb.n1 * cb.n2;
+    out->n_vis = cb.n_vis;
+    out->n_coef = cb.sara.I;
+    out->n_facet_pix = cb.n_facet_pix;
+    out->n_facets = cb.Qy * cb.Qx;
+    out->n_blocks = cb.L * cb.B;
+  });
+}
+
+fhs_status fhs_sync(fhs_ctx* ctx) {
+  return guarded(ctx, [&] { FHS_CUDA(cudaStreamSynchronize(ctx->stream)); });
+}
+
+const char* fhs_last_error(const fhs_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+fhs_status fhs_vis_permutation(const fhs_ctx* cctx, int32_t cube, int64_t* perm_host) {
+  fhs_ctx* ctx = const_cast<fhs_ctx*>(cctx);
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(perm_host, FHS_ERR_INVALID_ARG, "perm_host is NULL");
+    const Cube& cb = get_cube(ctx, cube);
+    memcpy(perm_host, cb.perm_host.data(), cb.n_vis * sizeof(int64_t));
+  });
+}
+
+fhs_status fhs_vis_to_internal(fhs_ctx* ctx, int32_t cube, const float* user, float* internal) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(user && internal && user != internal, FHS_ERR_INVALID_ARG, "need distinct non-NULL arrays");
+    const Cube& cb = get_cube(ctx, cube);
+    launch_vis_gather(cb.d_perm, cb.n_vis, (const float2*)user, (float2*)internal, ctx->stream);
+    check_launch("vis_to_internal");
+  });
+}
+
+fhs_status fhs_vis_to_user(fhs_ctx* ctx, int32_t cube, const float* internal, float* user) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(user && internal && user != internal, FHS_ERR_INVALID_ARG, "need distinct non-NULL arrays");
+    const Cube& cb = get_cube(ctx, cube);
+    launch_vis_scatter(cb.d_perm, cb.n_vis, (const float2*)internal, (float2*)user, ctx->stream);
+    check_launch("vis_to_user");
+  });
+}
+
+fhs_status fhs_measure(fhs_ctx* ctx, int32_t cube, const float* x, float* y) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(x && y, FHS_ERR_INVALID_ARG, "NULL array");
+    const Cube& cb = get_cube(ctx, cube);
+    launch_measure(ctx, cb, x, (float2*)y, ctx->stream);
+    check_launch("measure");
+  });
+}
+
+fhs_status fhs_adjoint(fhs_ctx* ctx, int32_t cube, const float* v, float* x) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(x && v, FHS_ERR_INVALID_ARG, "NULL array");
+    const Cube& cb = get_cube(ctx, cube);
+    adjoint_into(ctx, cb, (const float2*)v, nullptr, nullptr, x, nullptr, false);
+  });
+}
+
+fhs_status fhs_opnorm_sq(fhs_ctx* ctx, int32_t cube, int32_t max_iter, double rel_tol, double* out) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(out && max_iter >= 1, FHS_ERR_INVALID_ARG, "bad arguments");
+    const Cube& cb = get_cube(ctx, cube);
+    cudaStream_t st = ctx->stream;
+    const int L = cb.L;
+    const int64_t N = (int64_t)cb.n1 * cb.n2;
+    const int np = 64;
+    std::vector<float> ones(N, (float)(1.0 / sqrt((double)N)));
+    for (int l = 0; l < L; ++l) upload(ctx->s.img2 + l * N, ones.data(), N, st);
+    std::vector<double> val(L, 0.0), inv(L);
+    std::vector<char> done(L, 0);
+    double* dinv = ctx->s.blk_out + 2 * ctx->s.vis_elems * 0;   // reuse: first L doubles of blk_out tail
+    dinv = ctx->s.blk_out;
+    for (int it = 0; it < max_iter; ++it) {
+      launch_measure(ctx, cb, ctx->s.img2, ctx->s.vis, st);
+      adjoint_into(ctx, cb, ctx->s.vis, nullptr, nullptr, ctx->s.img, nullptr, false);
+      launch_sumsq(ctx->s.img, N, L, ctx->s.red, np, st);
+      check_launch("power method");
+      FHS_CUDA(cudaMemcpyAsync(ctx->s.red_host, ctx->s.red, (size_t)L * np * 2 * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+      FHS_CUDA(cudaStreamSynchronize(st));
+      bool all = true;
+      for (int l = 0; l < L; ++l) {
+        double s = 0.0;
+        for (int p = 0; p < np; ++p) s += ctx->s.red_host[2 * ((size_t)l * np + p)];
+        double nv = sqrt(s);
+        FHS_REQUIRE(std::isfinite(nv) && nv > 0, FHS_ERR_NONFINITE, "power method norm is not finite/positive");
+        if (!done[l] && val[l] > 0 && fabs(nv - val[l]) / nv < rel_tol) done[l] = 1;
+        val[l] = nv;
+        inv[l] = 1.0 / nv;
+        all = all && done[l];
+      }
+      if (all) break;
+      upload(dinv, inv.data(), L, st);
+      launch_scale_by_channel(ctx->s.img, N, L, dinv, st);
+      FHS_CUDA(cudaMemcpyAsync(ctx->s.img2, ctx->s.img, (size_t)L * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      check_launch("power method scale");
+    }
+    FHS_CUDA(cudaStreamSynchronize(st));
+    for (int l = 0; l < L; ++l) out[l] = val[l];
+  });
+}
+
+fhs_status fhs_sara_analysis(fhs_ctx* ctx, int32_t cube, const float* x, float* coef) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(x && coef, FHS_ERR_INVALID_ARG, "NULL array");
+    const Cube& cb = get_cube(ctx, cube);
+    launch_sara_analysis(ctx, cb, x, coef, ctx->stream);
+    check_launch("sara analysis");
+  });
+}
+
+fhs_status fhs_sara_synthesis(fhs_ctx* ctx, int32_t cube, const float* coef, float* x) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(x && coef, FHS_ERR_INVALID_ARG, "NULL array");
+    const Cube& cb = get_cube(ctx, cube);
+    launch_sara_synthesis(ctx, cb, coef, x, 1.f, false, ctx->stream);
+    check_launch("sara synthesis");
+  });
+}
+
+fhs_status fhs_prox_l21_sara_facets(fhs_ctx* ctx, int32_t cube, const float* xcheck, float* W, const float* theta,
+                                    float* A) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(xcheck && W && theta && A, FHS_ERR_INVALID_ARG, "NULL array");
+    const Cube& cb = get_cube(ctx, cube);
+    sara_dual(ctx, cb, xcheck, W, theta, A);
+  });
+}
+
+fhs_status fhs_prox_nuclear_facets(fhs_ctx* ctx, int32_t cube, const float* xcheck, float* P, const float* theta_bar,
+                                   float* A) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(xcheck && P && theta_bar && A, FHS_ERR_INVALID_ARG, "NULL array");
+    const Cube& cb = get_cube(ctx, cube);
+    launch_nuclear(ctx, cb, xcheck, P, theta_bar, A, false, nullptr, ctx->stream);
+    check_launch("nuclear dual");
+  });
+}
+
+fhs_status fhs_proj_l2ball_blocks(fhs_ctx* ctx, int32_t cube, const float* z, const float* y, float* v_out,
+                                  double* dnorm_out) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(z && y && v_out, FHS_ERR_INVALID_ARG, "NULL array");
+    const Cube& cb = get_cube(ctx, cube);
+    cudaStream_t st = ctx->stream;
+    int np = degrid_parts(cb);
+    launch_l2ball_partials(cb, (const float2*)z, (const float2*)y, ctx->s.vis, ctx->s.red, np, st);
+    launch_block_finalize(cb, ctx->s.red, np, ctx->s.blk_scale, ctx->s.blk_out, st);
+    launch_l2ball_scale(cb, ctx->s.vis, ctx->s.blk_scale, (float2*)v_out, st);
+    check_launch("l2 ball");
+    if (dnorm_out) {
+      FHS_CUDA(cudaMemcpyAsync(dnorm_out, ctx->s.blk_out, (size_t)cb.L * cb.B * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+      FHS_CUDA(cudaStreamSynchronize(st));
+      for (int k = 0; k < cb.L * cb.B; ++k)
+        FHS_REQUIRE(std::isfinite(dnorm_out[k]), FHS_ERR_NONFINITE, "non-finite block norm");
+    }
+  });
+}
+
+fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta, float* theta_bar) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(x && theta && theta_bar, FHS_ERR_INVALID_ARG, "NULL array");
+    const Cube& cb = get_cube(ctx, cube);
+    cudaStream_t st = ctx->stream;
+    launch_sara_analysis(ctx, cb, x, ctx->s.coef, st);
+    launch_l21_weights(cb, ctx->s.coef, theta, st);
+    launch_nuclear(ctx, cb, x, nullptr, nullptr, nullptr, true, theta_bar, st);
+    check_launch("reweight");
+  });
+}
+
+fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fhs_iter_stats* stats) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(it && n_iter >= 0, FHS_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t st = ctx->stream;
+    const int nc = (int)ctx->cubes.size();
+    for (int c = 0; c < nc; ++c) {
+      const fhs_iterate& a = it[c];
+      FHS_REQUIRE(a.X && a.Xcheck && a.y && a.state.W && a.state.theta && a.state.P && a.state.theta_bar &&
+                      a.state.v && a.state.u_prev,
+                  FHS_ERR_INVALID_ARG, "NULL array in fhs_iterate");
+    }
+    std::vector<double> primal_host, blk_host;
+    for (int p = 0; p < n_iter; ++p) {
+      const bool last = (p == n_iter - 1);
+      for (int c = 0; c < nc; ++c) {
+        const Cube& cb = ctx->cubes[c];
+        const fhs_iterate& a = it[c];
+        float* A = ctx->s.img;
+        const size_t nimg = (size_t)cb.L * cb.n1 * cb.n2;
+        FHS_CUDA(cudaMemsetAsync(A, 0, nimg * sizeof(float), st));
+        launch_nuclear(ctx, cb, a.Xcheck, a.state.P, a.state.theta_bar, A, false, nullptr, st);
+        check_launch("nuclear dual");
+        sara_dual(ctx, cb, a.Xcheck, a.state.W, a.state.theta, A);
+        // data fidelity: x_hat = F Z x, degrid + l2-ball duals, grid, adjoint
+        launch_fft_forward(ctx, cb, a.X, ctx->s.grid, st);
+        int np = degrid_parts(cb);
+        launch_degrid_pdfb(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
+                           (float2*)a.state.u_prev, ctx->s.red, np, st);
+        launch_block_finalize(cb, ctx->s.red, np, ctx->s.blk_scale, ctx->s.blk_out, st);
+        adjoint_into(ctx, cb, ctx->s.vis, ctx->s.blk_scale, (float2*)a.state.v, A, cb.d_eta, true);
+        // primal update
+        int pp = primal_parts(cb);
+        launch_primal(cb, a.X, a.Xcheck, A, ctx->s.red, pp, st);
+        check_launch("primal");
+        if (last && stats) {
+          primal_host.resize(2 * pp);
+          blk_host.resize(2 * cb.L * cb.B);
+          FHS_CUDA(cudaMemcpyAsync(primal_host.data(), ctx->s.red, 2 * pp * sizeof(double), cudaMemcpyDeviceToHost, st));
+          FHS_CUDA(cudaMemcpyAsync(blk_host.data(), ctx->s.blk_out, 2 * cb.L * cb.B * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+          FHS_CUDA(cudaStreamSynchronize(st));
+          double dx2 = 0.0, x2 = 0.0;
+          for (int k = 0; k < pp; ++k) { dx2 += primal_host[2 * k]; x2 += primal_host[2 * k + 1]; }
+          double r2 = 0.0, e2 = 0.0;
+          for (int k = 0; k < cb.L * cb.B; ++k) {
+            r2 += blk_host[cb.L * cb.B + k] * blk_host[cb.L * cb.B + k];
+            e2 += cb.eps[k] * cb.eps[k];
+          }
+          FHS_REQUIRE(std::isfinite(dx2) && std::isfinite(x2) && std::isfinite(r2), FHS_ERR_NONFINITE,
+                      "non-finite iteration statistics");
+          stats[c].xi = x2 > 0 ? sqrt(dx2 / x2) : INFINITY;
+          stats[c].res_norm = sqrt(r2);
+          stats[c].eps_norm = sqrt(e2);
+        }
+      }
+    }
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+// Reweighted nuclear-norm duals of the apodised facets (Algorithm 2 P update,
+// Table 2 row 2) on GB300.
+//
+// For facet q with Z_q = P_q + D_q S~_q Xcheck (N~_q x L):
+//   (I - prox_{alpha ||.||_*,theta})(Z) = U diag(min(s_j, alpha_j)) V^T = Z V diag(m) V^T,
+//   m_j = min(1, alpha_j / s_j), Z^T Z = V diag(s^2) V^T.
+// Three kernels:
+//   k_gram   : partial Gram matrices Z^T Z of pixel chunks (FP32, staged in smem);
+//   k_eig    : FP64 sum of the partials in fixed order, cyclic Jacobi
+//              eigen-solve of the L x L Gram, M_q = V diag(m) V^T (or weights);
+//   k_apply  : pixel-driven: for each pixel and each facet covering it,
+//              P_q <- Z_q M_q and A += zeta D_q P_q (every A pixel written once).
+#include <cuda_runtime.h>
+
+#include "fhs_internal.h"
+
+namespace fhs {
+
+constexpr int kGramChunk = 1024;   // pixels per Gram partial
+constexpr int kGramSub = 64;       // pixels staged in shared memory at a time
+
+__device__ __forceinline__ float facet_weight(const NucFacet& f, const float* __restrict__ win, int rr, int cc) {
+  return win[f.wy_off + rr] * win[f.wx_off + cc];
+}
+
+// Partial Gram of chunk blockIdx.x of facet blockIdx.y.  Thread owns an
+// LB x LB block of G; Lp = L rounded up to a multiple of LB.
+template <int LB>
+__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, const float* __restrict__ P,
+                                              const NucFacet* __restrict__ facets, const float* __restrict__ win,
+                                              int n1, int n2, int L, int use_P, float* __restrict__ part,
+                                              int nchunk_max) {
+  __shared__ float z[kGramSub][kMaxL + 1];
+  const int q = blockIdx.y;
+  const NucFacet f = facets[q];
+  const int h = f.r1 - f.r0, w = f.c1 - f.c0;
+  const int Nq = h * w;
+  const int p0 = blockIdx.x * kGramChunk;
+  if (p0 >= Nq) return;
+  const int p1 = min(Nq, p0 + kGramChunk);
+  const int Lp = (L + LB - 1) / LB * LB;
+  const int nb = Lp / LB;
+  const int ta = threadIdx.x / nb, tb = threadIdx.x % nb;
+  const bool active = ta < nb;
+  float acc[LB][LB];
+#pragma unroll
+  for (int i = 0; i < LB; ++i)
+#pragma unroll
+    for (int j = 0; j < LB; ++j) acc[i][j] = 0.f;
+  const size_t N = (size_t)n1 * n2;
+  for (int s0 = p0; s0 < p1; s0 += kGramSub) {
+    for (int idx = threadIdx.x; idx < kGramSub * Lp; idx += blockDim.x) {
+      int pix = idx % kGramSub, l = idx / kGramSub;
+      int p = s0 + pix;
+      float val = 0.f;
+      if (p < p1 && l < L) {
+        int rr = p / w, cc = p % w;
+        float d = facet_weight(f, win, rr, cc);
+        val = d * xc[l * N + (size_t)(f.r0 + rr) * n2 + (f.c0 + cc)];
+        if (use_P) val += P[f.p_off + (size_t)l * Nq + p];
+      }
+      z[pix][l] = val;
+    }
+    __syncthreads();
+    if (active) {
+      for (int pix = 0; pix < kGramSub; ++pix) {
+        float a[LB], b[LB];
+#pragma unroll
+        for (int i = 0; i < LB; ++i) a[i] = z[pix][ta * LB + i];
+#pragma unroll
+        for (int j = 0; j < LB; ++j) b[j] = z[pix][tb * LB + j];
+#pragma unroll
+        for (int i = 0; i < LB; ++i)
+#pragma unroll
+          for (int j = 0; j < LB; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (active) {
+    float* out = part + ((size_t)q * nchunk_max + blockIdx.x) * L * L;
+#pragma unroll
+    for (int i = 0; i < LB; ++i)
+#pragma unroll
+      for (int j = 0; j < LB; ++j) {
+        int a = ta * LB + i, b = tb * LB + j;
+        if (a < L && b < L) out[a * L + b] = acc[i][j];
+      }
+  }
+}
+
+// One warp per facet: G = sum of partial Grams (FP64, fixed order), cyclic
+// Jacobi eigen-decomposition G = V diag(lambda) V^T, s = sqrt(max(lambda, 0))
+// sorted descending, then either M = V diag(m) V^T with
+// m_j = min(1, alpha_j / s_j), alpha_j = (mu_bar_q / zeta) theta_bar_q[rank j]
+// (dual mode), or theta_bar_q[rank] = mu_bar_q / (s + mu_bar_q) (weights mode).
+__global__ void __launch_bounds__(32) k_eig(const float* __restrict__ part, int nchunk_max,
+                                            const NucFacet* __restrict__ facets, int L,
+                                            const float* __restrict__ theta_bar, const float* __restrict__ mubar,
+                                            float inv_zeta, float* __restrict__ Mout, float* __restrict__ tb_out,
+                                            int weights_mode, int max_sweeps) {
+  extern __shared__ double sh[];
+  const int Ls = L + 1;
+  double* G = sh;                 // [L][L+1]
+  double* V = sh + L * Ls;        // [L][L+1]
+  double* lam = V + L * Ls;       // [L]
+  int* rank = (int*)(lam + L);    // [L]
+  const int q = blockIdx.x, lane = threadIdx.x;
+  const NucFacet f = facets[q];
+  const int Nq = (f.r1 - f.r0) * (f.c1 - f.c0);
+  const int nch = (Nq + kGramChunk - 1) / kGramChunk;
+  for (int idx = lane; idx < L * L; idx += 32) {
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += (double)part[((size_t)q * nchunk_max + c) * L * L + idx];
+    int a = idx / L, b = idx % L;
+    G[a * Ls + b] = s;
+    V[a * Ls + b] = (a == b) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  // symmetrise (the partial Grams are symmetric up to rounding order)
+  for (int idx = lane; idx < L * L; idx += 32) {
+    int a = idx / L, b = idx % L;
+    if (a < b) {
+      double m = 0.5 * (G[a * Ls + b] + G[b * Ls + a]);
+      G[a * Ls + b] = m;
+      G[b * Ls + a] = m;
+    }
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int idx = lane; idx < L * L; idx += 32) {
+      int a = idx / L, b = idx % L;
+      double g = G[a * Ls + b];
+      if (a == b) dia += g * g; else off += g * g;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if (off <= 1e-30 * dia || off == 0.0) break;
+    for (int p = 0; p < L - 1; ++p) {
+      for (int r = p + 1; r < L; ++r) {
+        double gpr = G[p * Ls + r];
+        double gpp = G[p * Ls + p], grr = G[r * Ls + r];
+        if (fabs(gpr) <= 1e-300 || fabs(gpr) <= 1e-18 * sqrt(fabs(gpp * grr))) continue;
+        double th = (grr - gpp) / (2.0 * gpr);
+        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+        double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        __syncwarp();
+        for (int k = lane; k < L; k += 32) {     // rows p, r
+          double a = G[p * Ls + k], b = G[r * Ls + k];
+          G[p * Ls + k] = c * a - s * b;
+          G[r * Ls + k] = s * a + c * b;
+        }
+        __syncwarp();
+        for (int k = lane; k < L; k += 32) {     // columns p, r and eigenvectors
+          double a = G[k * Ls + p], b = G[k * Ls + r];
+          G[k * Ls + p] = c * a - s * b;
+          G[k * Ls + r] = s * a + c * b;
+          double va = V[k * Ls + p], vb = V[k * Ls + r];
+          V[k * Ls + p] = c * va - s * vb;
+          V[k * Ls + r] = s * va + c * vb;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  for (int j = lane; j < L; j += 32) lam[j] = G[j * Ls + j];
+  __syncwarp();
+  for (int j = lane; j < L; j += 32) {
+    int rk = 0;
+    for (int k = 0; k < L; ++k) rk += (lam[k] > lam[j]) || (lam[k] == lam[j] && k < j);
+    rank[j] = rk;
+  }
+  __syncwarp();
+  const float mb = mubar[q];
+  if (weights_mode) {
+    for (int j = lane; j < L; j += 32) {
+      double s = sqrt(fmax(lam[j], 0.0));
+      tb_out[(size_t)q * L + rank[j]] = (float)((double)mb / (s + (double)mb));
+    }
+    return;
+  }
+  // m_j stored in lam
+  __syncwarp();
+  for (int j = lane; j < L; j += 32) {
+    double s = sqrt(fmax(lam[j], 0.0));
+    double alpha = (double)mb * (double)inv_zeta * (double)theta_bar[(size_t)q * L + rank[j]];
+    lam[j] = (s > alpha) ? alpha / s : 1.0;
+  }
+  __syncwarp();
+  for (int idx = lane; idx < L * L; idx += 32) {
+    int a = idx / L, b = idx % L;
+    double m = 0.0;
+    for (int j = 0; j < L; ++j) m += V[a * Ls + j] * lam[j] * V[b * Ls + j];
+    Mout[(size_t)q * L * L + idx] = (float)m;
+  }
+}
+
+// Pixel-driven update: each thread owns one pixel; for every facet covering it,
+// z = P_q + D_q x, P_q <- z M_q, A += zeta D_q P_q.
+template <int LMAX>
+__global__ void __launch_bounds__(256) k_apply(const float* __restrict__ xc, float* __restrict__ P,
+                                               const NucFacet* __restrict__ facets, const float* __restrict__ win,
+                                               const float* __restrict__ M, int n1, int n2, int L, int Qy, int Qx,
+                                               const int* __restrict__ ty_of, const int* __restrict__ tx_of,
+                                               float zeta, float* __restrict__ A) {
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int r = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (r >= n1 || c >= n2) return;
+  const size_t N = (size_t)n1 * n2;
+  const size_t pix = (size_t)r * n2 + c;
+  float x[LMAX], acc[LMAX];
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    x[l] = (l < L) ? xc[l * N + pix] : 0.f;
+    acc[l] = 0.f;
+  }
+  const int ty = ty_of[r], tx = tx_of[c];
+  for (int dy = 0; dy < 2; ++dy) {
+    int qy = ty + dy;
+    if (qy >= Qy) break;
+    for (int dx = 0; dx < 2; ++dx) {
+      int qx = tx + dx;
+      if (qx >= Qx) break;
+      const NucFacet f = facets[qy * Qx + qx];
+      if (r < f.r0 || r >= f.r1 || c < f.c0 || c >= f.c1) continue;
+      const int w = f.c1 - f.c0;
+      const int Nq = (f.r1 - f.r0) * w;
+      const int p = (r - f.r0) * w + (c - f.c0);
+      const float d = facet_weight(f, win, r - f.r0, c - f.c0);
+      float* Pq = P + f.p_off;
+      float z[LMAX];
+#pragma unroll
+      for (int l = 0; l < LMAX; ++l) z[l] = (l < L) ? fmaf(d, x[l], Pq[(size_t)l * Nq + p]) : 0.f;
+      const float* Mq = M + (size_t)(qy * Qx + qx) * L * L;
+#pragma unroll
+      for (int b = 0; b < LMAX; ++b) {
+        if (b < L) {
+          float s = 0.f;
+#pragma unroll
+          for (int a = 0; a < LMAX; ++a)
+            if (a < L) s = fmaf(z[a], __ldg(&Mq[a * L + b]), s);
+          Pq[(size_t)b * Nq + p] = s;
+          acc[b] = fmaf(zeta * d, s, acc[b]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l)
+    if (l < L) A[l * N + pix] += acc[l];
+}
+
+static int nchunk_max(const Cube& cb) { return (cb.max_facet_pix + kGramChunk - 1) / kGramChunk; }
+
+void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P, const float* theta_bar, float* A,
+                    bool weights_mode, float* theta_bar_out, cudaStream_t st) {
+  const int L = cb.L;
+  const int Q = cb.Qy * cb.Qx;
+  const int nch = nchunk_max(cb);
+  dim3 gg(nch, Q);
+  int use_P = (P != nullptr && !weights_mode) ? 1 : 0;
+  if (L <= 16) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  else if (L <= 32) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  else k_gram<4><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  size_t sm = (size_t)2 * L * (L + 1) * sizeof(double) + L * sizeof(double) + L * sizeof(int);
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024); attr = true; }
+  k_eig<<<Q, 32, sm, st>>>(ctx->s.gram, nch, cb.d_facets, L, theta_bar, cb.d_mubar, (float)(1.0 / cb.zeta),
+                           ctx->s.nucM, theta_bar_out, weights_mode ? 1 : 0, 40);
+  if (weights_mode) return;
+  dim3 ga((cb.n2 + 31) / 32, (cb.n1 + 7) / 8);
+  const int* tyo = cb.d_tile_of;
+  const int* txo = cb.d_tile_of + cb.n1;
+  float zeta = (float)cb.zeta;
+  if (L <= 16) k_apply<16><<<ga, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, ctx->s.nucM, cb.n1, cb.n2, L, cb.Qy, cb.Qx, tyo, txo, zeta, A);
+  else if (L <= 32) k_apply<32><<<ga, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, ctx->s.nucM, cb.n1, cb.n2, L, cb.Qy, cb.Qx, tyo, txo, zeta, A);
+  else k_apply<64><<<ga, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, ctx->s.nucM, cb.n1, cb.n2, L, cb.Qy, cb.Qx, tyo, txo, zeta, A);
+}
+
+}  // namespace fhs

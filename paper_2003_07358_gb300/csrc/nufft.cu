@@ -1,0 +1,693 @@
+// Measurement operator Phi = G F Z (Eq. 1) and its adjoint on GB300:
+//  * Z + row DFT fused: one CTA transforms S grid rows held in shared memory
+//    (Stockham autosort, radix 8/4/2, twiddles from an exp(-2 pi i k / Kmax) table);
+//  * column DFT over 2n1 rows as one pass (2n1 <= 1024) or two passes of the
+//    four-step factorisation K1 = N1c * N2c; the second pass leaves the rows
+//    in digit-reversed order (frequency k1 + N1c k2 at row N2c k1 + k2),
+//    which the interpolation kernels index directly, so no transpose pass;
+//  * zero rows of the padded image are never read (pruned first column pass),
+//    and the adjoint stores only the rows that survive the crop;
+//  * G: one thread per visibility gathers the 7x7 Kaiser-Bessel taps; weights
+//    from per-tap degree-11 polynomials fitted at context creation;
+//  * G^T: one CTA per 64x64 grid tile accumulates in shared memory the
+//    visibilities whose footprint touches the tile (its own sorted bin plus the
+//    crossing classes of its 3 upper/left neighbours) and writes every grid
+//    cell exactly once: no global atomics;
+//  * l2-ball data duals (Table 2 row 4) fused into the degridder; block norms
+//    in FP64 with a fixed-order two-stage reduction.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "fhs_internal.h"
+
+namespace fhs {
+
+__constant__ KbPoly c_kb;
+
+cudaError_t upload_kb_poly(const KbPoly& p) { return cudaMemcpyToSymbol(c_kb, &p, sizeof(p)); }
+
+// ------------------------------------------------------------------ complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// ----------------------------------------------------------- R-point DFTs
+// Forward sign exp(-2 pi i / R); `inv` flips the sign (unnormalised).
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3, bool inv) {
+  float2 a0 = cadd(x0, x2), a1 = csub(x0, x2), a2 = cadd(x1, x3), a3 = csub(x1, x3);
+  // -i * a3 = (a3.y, -a3.x)
+  float2 mia3 = inv ? make_float2(-a3.y, a3.x) : make_float2(a3.y, -a3.x);
+  x0 = cadd(a0, a2);
+  x2 = csub(a0, a2);
+  x1 = cadd(a1, mia3);
+  x3 = csub(a1, mia3);
+}
+
+__device__ __forceinline__ void dft8(float2* v, bool inv) {
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4(e0, e1, e2, e3, inv);
+  dft4(o0, o1, o2, o3, inv);
+  const float c = 0.70710678118654752440f;
+  float sg = inv ? 1.f : -1.f;
+  // w^1 = (c, sg c), w^2 = (0, sg), w^3 = (-c, sg c)
+  float2 t1 = cmul(o1, make_float2(c, sg * c));
+  float2 t2 = cmul(o2, make_float2(0.f, sg));
+  float2 t3 = cmul(o3, make_float2(-c, sg * c));
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, t1); v[5] = csub(e1, t1);
+  v[2] = cadd(e2, t2); v[6] = csub(e2, t2);
+  v[3] = cadd(e3, t3); v[7] = csub(e3, t3);
+}
+
+template <int R>
+__device__ __forceinline__ void dftR(float2* v, bool inv) {
+  if constexpr (R == 2) dft2(v[0], v[1]);
+  else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3], inv);
+  else dft8(v, inv);
+}
+
+// One Stockham autosort pass over S interleaved sequences of length N held in
+// shared memory as buf[n * S + s].  NT threads, each owning (N/R)*S/NT butterflies.
+template <int N, int S, int NT, int R>
+__device__ __forceinline__ void stockham_pass(float2* buf, int Ns, const float2* __restrict__ tw,
+                                              int twstride, bool inv) {
+  constexpr int NB = (N / R) * S;
+  constexpr int PER = NB / NT;
+  static_assert(PER >= 1 && PER * NT == NB, "thread count must divide the butterflies");
+  float2 v[PER][R];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    int item = threadIdx.x + p * NT;
+    int s = item % S, j = item / S;
+    int k = j % Ns;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[p][r] = buf[(j + r * (N / R)) * S + s];
+    if (Ns > 1) {
+      int step = (N / (Ns * R)) * twstride;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(&tw[r * k * step]);
+        v[p][r] = cmul(v[p][r], inv ? cconj(w) : w);
+      }
+    }
+    dftR<R>(v[p], inv);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    int item = threadIdx.x + p * NT;
+    int s = item % S, j = item / S;
+    int k = j % Ns;
+    int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[(base + r * Ns) * S + s] = v[p][r];
+  }
+  __syncthreads();
+}
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+// In-place DFT of S interleaved length-N sequences in shared memory.
+// twstride = Kmax / N (table holds exp(-2 pi i k / Kmax)).
+template <int N, int S, int NT>
+__device__ __forceinline__ void smem_fft(float2* buf, const float2* __restrict__ tw, int twstride, bool inv) {
+  constexpr int LOG = ilog2c(N);
+  int Ns = 1;
+#pragma unroll 1
+  for (int p = 0; p < LOG / 3; ++p) {
+    stockham_pass<N, S, NT, 8>(buf, Ns, tw, twstride, inv);
+    Ns *= 8;
+  }
+  if constexpr (LOG % 3 == 2) stockham_pass<N, S, NT, 4>(buf, Ns, tw, twstride, inv);
+  if constexpr (LOG % 3 == 1) stockham_pass<N, S, NT, 2>(buf, Ns, tw, twstride, inv);
+}
+
+// sequences per CTA for row transforms and columns per CTA for column transforms
+template <int N> struct RowCfg { static constexpr int S = N >= 2048 ? 1 : 2048 / N; static constexpr int NT = N * S / 16; };
+template <int N> struct ColCfg { static constexpr int W = N <= 512 ? 32 : 16; static constexpr int NT = N * W / 16; };
+
+// Physical row of frequency row k when the column DFT used two passes.
+__device__ __forceinline__ int phys_row(int k, int N1c, int N2c) { return (k % N1c) * N2c + k / N1c; }
+
+// ------------------------------------------------------------ row kernels
+// Z then row DFT: pixel rows r0..r0+S-1 of channel blockIdx.y -> grid rows (r - n1/2) mod K1.
+template <int N>
+__global__ void __launch_bounds__(RowCfg<N>::NT) k_row_fwd(const float* __restrict__ x, float2* __restrict__ grid,
+                                                           const float* __restrict__ sr, const float* __restrict__ sc,
+                                                           const float2* __restrict__ tw, int twstride, int n1, int n2,
+                                                           int K1) {
+  constexpr int S = RowCfg<N>::S, NT = RowCfg<N>::NT;
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  const int l = blockIdx.y;
+  const int r0 = blockIdx.x * S;
+  const float* xl = x + (size_t)l * n1 * n2;
+  const int h2 = n2 / 2;
+  for (int idx = threadIdx.x; idx < N * S; idx += NT) {
+    int s = idx / N, n = idx % N;
+    int r = r0 + s;
+    int c = n < h2 ? n + h2 : (n >= N - h2 ? n - (N - h2) : -1);
+    float val = 0.f;
+    if (c >= 0 && r < n1) val = xl[(size_t)r * n2 + c] * sr[r] * sc[c];
+    buf[n * S + s] = make_float2(val, 0.f);
+  }
+  __syncthreads();
+  smem_fft<N, S, NT>(buf, tw, twstride, false);
+  for (int idx = threadIdx.x; idx < N * S; idx += NT) {
+    int s = idx / N, n = idx % N;
+    int r = r0 + s;
+    if (r >= n1) continue;
+    int g = (r - n1 / 2 + K1) % K1;
+    grid[((size_t)l * K1 + g) * N + n] = buf[n * S + s];
+  }
+}
+
+// Inverse row DFT of the grid rows that survive the crop, then crop, Z^T, real part:
+// out[l][r][c] (+)= eta_l * s_r * s_c * Re(...)
+template <int N>
+__global__ void __launch_bounds__(RowCfg<N>::NT) k_row_adj(const float2* __restrict__ grid, float* __restrict__ out,
+                                                           const float* __restrict__ sr, const float* __restrict__ sc,
+                                                           const float* __restrict__ eta, int accumulate,
+                                                           const float2* __restrict__ tw, int twstride, int n1, int n2,
+                                                           int K1) {
+  constexpr int S = RowCfg<N>::S, NT = RowCfg<N>::NT;
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  const int l = blockIdx.y;
+  const int r0 = blockIdx.x * S;
+  for (int idx = threadIdx.x; idx < N * S; idx += NT) {
+    int s = idx / N, n = idx % N;
+    int r = r0 + s;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < n1) {
+      int g = (r - n1 / 2 + K1) % K1;
+      v = grid[((size_t)l * K1 + g) * N + n];
+    }
+    buf[n * S + s] = v;
+  }
+  __syncthreads();
+  smem_fft<N, S, NT>(buf, tw, twstride, true);
+  const float e = eta ? eta[l] : 1.f;
+  const int h2 = n2 / 2;
+  float* ol = out + (size_t)l * n1 * n2;
+  for (int idx = threadIdx.x; idx < n2 * S; idx += NT) {
+    int s = idx / n2, c = idx % n2;
+    int r = r0 + s;
+    if (r >= n1) continue;
+    int n = (c - h2 + N) % N;
+    float val = e * sr[r] * sc[c] * buf[n * S + s].x;
+    size_t o = (size_t)r * n2 + c;
+    ol[o] = accumulate ? ol[o] + val : val;
+  }
+}
+
+// -------------------------------------------------------- column kernel
+// One pass of the column DFT: for group g = blockIdx.y, loads rows
+// row(i) = g * gmul + i * istride (i < N), columns [c0, c0 + W), transforms
+// along i, optional twiddle exp(-+2 pi i g i / K1) after (forward) or before
+// (inverse) the transform, and stores back to the same rows.
+// prune: rows outside the non-zero band of the zero-padded image are treated as
+// zero on load (forward) or not stored (inverse).
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::NT) k_col(float2* __restrict__ grid, int K1, int K2, int gmul,
+                                                       int istride, int twiddle, int inv, int prune, int n1,
+                                                       const float2* __restrict__ tw, int twstrideN, int twstrideK) {
+  constexpr int W = ColCfg<N>::W, NT = ColCfg<N>::NT;
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  const int l = blockIdx.z;
+  const int g = blockIdx.y;
+  const int c0 = blockIdx.x * W;
+  float2* gl = grid + (size_t)l * K1 * K2;
+  const int h1 = n1 / 2;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    int i = idx / W, w = idx % W;
+    int row = g * gmul + i * istride;
+    bool zero = prune && !inv && (row >= h1 && row < K1 - h1);
+    float2 v = zero ? make_float2(0.f, 0.f) : gl[(size_t)row * K2 + c0 + w];
+    if (twiddle && inv) {
+      float2 t = __ldg(&tw[(size_t)((g * i) % K1) * twstrideK]);
+      v = cmul(v, cconj(t));
+    }
+    buf[i * W + w] = v;
+  }
+  __syncthreads();
+  smem_fft<N, W, NT>(buf, tw, twstrideN, inv != 0);
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    int i = idx / W, w = idx % W;
+    int row = g * gmul + i * istride;
+    if (prune && inv && (row >= h1 && row < K1 - h1)) continue;
+    float2 v = buf[i * W + w];
+    if (twiddle && !inv) {
+      float2 t = __ldg(&tw[(size_t)((g * i) % K1) * twstrideK]);
+      v = cmul(v, t);
+    }
+    gl[(size_t)row * K2 + c0 + w] = v;
+  }
+}
+
+// ----------------------------------------------------------- dispatchers
+template <int N>
+static void row_fwd_n(const Cube& cb, const float* x, float2* grid, const float2* tw, int Kmax, cudaStream_t st) {
+  constexpr int S = RowCfg<N>::S, NT = RowCfg<N>::NT;
+  size_t sm = (size_t)N * S * sizeof(float2);
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_row_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
+  dim3 grd((cb.n1 + S - 1) / S, cb.L);
+  k_row_fwd<N><<<grd, NT, sm, st>>>(x, grid, cb.d_scale_r, cb.d_scale_c, tw, Kmax / N, cb.n1, cb.n2, cb.K1);
+}
+
+template <int N>
+static void row_adj_n(const Cube& cb, const float2* grid, float* out, const float* eta, bool acc, const float2* tw,
+                      int Kmax, cudaStream_t st) {
+  constexpr int S = RowCfg<N>::S, NT = RowCfg<N>::NT;
+  size_t sm = (size_t)N * S * sizeof(float2);
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_row_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
+  dim3 grd((cb.n1 + S - 1) / S, cb.L);
+  k_row_adj<N><<<grd, NT, sm, st>>>(grid, out, cb.d_scale_r, cb.d_scale_c, eta, acc ? 1 : 0, tw, Kmax / N, cb.n1,
+                                    cb.n2, cb.K1);
+}
+
+template <int N>
+static void col_n(const Cube& cb, float2* grid, int ngroups, int gmul, int istride, int twiddle, int inv, int prune,
+                  const float2* tw, int Kmax, cudaStream_t st) {
+  constexpr int W = ColCfg<N>::W, NT = ColCfg<N>::NT;
+  size_t sm = (size_t)N * W * sizeof(float2);
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_col<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
+  dim3 grd(cb.K2 / W, ngroups, cb.L);
+  k_col<N><<<grd, NT, sm, st>>>(grid, cb.K1, cb.K2, gmul, istride, twiddle, inv, prune, cb.n1, tw, Kmax / N,
+                                Kmax / cb.K1);
+}
+
+#define FHS_POW2_SWITCH(n, FN, ...)                  \
+  switch (n) {                                       \
+    case 32: FN<32>(__VA_ARGS__); break;             \
+    case 64: FN<64>(__VA_ARGS__); break;             \
+    case 128: FN<128>(__VA_ARGS__); break;           \
+    case 256: FN<256>(__VA_ARGS__); break;           \
+    case 512: FN<512>(__VA_ARGS__); break;           \
+    case 1024: FN<1024>(__VA_ARGS__); break;         \
+    case 2048: FN<2048>(__VA_ARGS__); break;         \
+    case 4096: FN<4096>(__VA_ARGS__); break;         \
+    case 8192: FN<8192>(__VA_ARGS__); break;         \
+    default: break;                                  \
+  }
+
+#define FHS_COL_SWITCH(n, FN, ...)                   \
+  switch (n) {                                       \
+    case 16: FN<16>(__VA_ARGS__); break;             \
+    case 32: FN<32>(__VA_ARGS__); break;             \
+    case 64: FN<64>(__VA_ARGS__); break;             \
+    case 128: FN<128>(__VA_ARGS__); break;           \
+    case 256: FN<256>(__VA_ARGS__); break;           \
+    case 512: FN<512>(__VA_ARGS__); break;           \
+    case 1024: FN<1024>(__VA_ARGS__); break;         \
+    default: break;                                  \
+  }
+
+void launch_fft_forward(fhs_ctx* ctx, const Cube& cb, const float* x, float2* grid, cudaStream_t st) {
+  FHS_POW2_SWITCH(cb.K2, row_fwd_n, cb, x, grid, ctx->d_tw, ctx->Kmax, st);
+  // step A: groups g < N2c, rows N2c*i + g; twiddle after unless single pass
+  FHS_COL_SWITCH(cb.N1c, col_n, cb, grid, cb.N2c, 1, cb.N2c, cb.N2c > 1 ? 1 : 0, 0, 1, ctx->d_tw, ctx->Kmax, st);
+  if (cb.N2c > 1) {
+    // step B: groups k1 < N1c, rows N2c*k1 + i
+    FHS_COL_SWITCH(cb.N2c, col_n, cb, grid, cb.N1c, cb.N2c, 1, 0, 0, 0, ctx->d_tw, ctx->Kmax, st);
+  }
+}
+
+void launch_fft_adjoint(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta, bool accumulate,
+                        cudaStream_t st) {
+  if (cb.N2c > 1) {
+    FHS_COL_SWITCH(cb.N2c, col_n, cb, grid, cb.N1c, cb.N2c, 1, 0, 1, 0, ctx->d_tw, ctx->Kmax, st);
+  }
+  FHS_COL_SWITCH(cb.N1c, col_n, cb, grid, cb.N2c, 1, cb.N2c, cb.N2c > 1 ? 1 : 0, 1, 1, ctx->d_tw, ctx->Kmax, st);
+  FHS_POW2_SWITCH(cb.K2, row_adj_n, cb, grid, out, eta, accumulate, ctx->d_tw, ctx->Kmax, st);
+}
+
+// ------------------------------------------------------ Kaiser-Bessel taps
+struct TapConst {
+  float hi_r, lo_r, hi_c, lo_c;   // K / (2 pi) split into two floats, rows and columns
+};
+
+__host__ __device__ inline TapConst tap_const(int K1, int K2) {
+  double cr = (double)K1 / (2.0 * 3.14159265358979323846);
+  double cc = (double)K2 / (2.0 * 3.14159265358979323846);
+  TapConst t;
+  t.hi_r = (float)cr; t.lo_r = (float)(cr - (double)t.hi_r);
+  t.hi_c = (float)cc; t.lo_c = (float)(cc - (double)t.hi_c);
+  return t;
+}
+
+// First tap k0 = floor(t - 3.5) + 1 and the 7 weights phi(t - k0 - j), t = omega * (hi + lo).
+// k0 depends only on p = fl(omega * hi) so that host and device agree exactly.
+__device__ __forceinline__ int kb_weights(float om, float hi, float lo, float* w) {
+  float p = __fmul_rn(om, hi);
+  float e = __fadd_rn(__fmaf_rn(om, hi, -p), __fmul_rn(om, lo));
+  float fl = floorf(__fadd_rn(p, -3.5f));
+  int k0 = (int)fl + 1;
+  float f = __fadd_rn(__fadd_rn(__fadd_rn(p, -(float)k0), -2.5f), e);
+  float xx = 2.f * f - 1.f;
+#pragma unroll
+  for (int j = 0; j < kTaps; ++j) {
+    float acc = c_kb.c[j][kPolyDeg];
+#pragma unroll
+    for (int d = kPolyDeg - 1; d >= 0; --d) acc = fmaf(acc, xx, c_kb.c[j][d]);
+    w[j] = acc;
+  }
+  return k0;
+}
+
+// --------------------------------------------------------- degridding G
+struct VisGeom {
+  int K1, K2, N1c, N2c;
+  TapConst tc;
+};
+
+__device__ __forceinline__ float2 degrid_one(const float2* __restrict__ g, float2 uv, const VisGeom& vg) {
+  float wr[kTaps], wc[kTaps];
+  int kr = kb_weights(uv.y, vg.tc.hi_r, vg.tc.lo_r, wr);
+  int kc = kb_weights(uv.x, vg.tc.hi_c, vg.tc.lo_c, wc);
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int a = 0; a < kTaps; ++a) {
+    int row = phys_row((kr + a) & (vg.K1 - 1), vg.N1c, vg.N2c);
+    const float2* gr = g + (size_t)row * vg.K2;
+    float2 racc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < kTaps; ++b) {
+      float2 v = __ldg(&gr[(kc + b) & (vg.K2 - 1)]);
+      racc.x = fmaf(wc[b], v.x, racc.x);
+      racc.y = fmaf(wc[b], v.y, racc.y);
+    }
+    acc.x = fmaf(wr[a], racc.x, acc.x);
+    acc.y = fmaf(wr[a], racc.y, acc.y);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ grid, const float2* __restrict__ uv,
+                                                float2* __restrict__ out, const int64_t* __restrict__ vis_off,
+                                                VisGeom vg) {
+  const int l = blockIdx.y;
+  int64_t i = vis_off[l] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= vis_off[l + 1]) return;
+  out[i] = degrid_one(grid + (size_t)l * vg.K1 * vg.K2, uv[i], vg);
+}
+
+// Deterministic CTA reduction of per-block sums: values v0 (||z-y||^2) and v1
+// (||y - u||^2) of the visibility handled by this thread, block id b.
+template <int NW>
+__device__ __forceinline__ void block_partials(double v0, double v1, int b, bool valid, int B, double* sred,
+                                               double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int b0 = __shfl_sync(0xffffffffu, valid ? b : -1, 0);
+  // lanes with invalid entries contribute zero to any block
+  bool uniform = __all_sync(0xffffffffu, !valid || b == b0) && b0 >= 0;
+  for (int k = threadIdx.x; k < NW * 2 * B; k += blockDim.x) sred[k] = 0.0;
+  __syncthreads();
+  if (uniform) {
+    double s0 = valid ? v0 : 0.0, s1 = valid ? v1 : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+      sred[(wid * 2 + 0) * B + b0] = s0;
+      sred[(wid * 2 + 1) * B + b0] = s1;
+    }
+  } else {
+    for (int bb = 0; bb < B; ++bb) {
+      double s0 = (valid && b == bb) ? v0 : 0.0, s1 = (valid && b == bb) ? v1 : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      if (lane == 0) {
+        sred[(wid * 2 + 0) * B + bb] = s0;
+        sred[(wid * 2 + 1) * B + bb] = s1;
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * B; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < NW; ++w) s += sred[w * 2 * B + k];
+    out[k] = s;
+  }
+}
+
+// Degrid + l2-ball data dual: u = G x_hat, z = v + 2u - u_prev, d = z - y;
+// per-block FP64 partial sums of ||d||^2 and ||y - u||^2; u_prev <- u.
+__global__ void __launch_bounds__(256) k_degrid_pdfb(const float2* __restrict__ grid, const float2* __restrict__ uv,
+                                                     const float2* __restrict__ y, const float2* __restrict__ v,
+                                                     float2* __restrict__ d_out, float2* __restrict__ u_prev,
+                                                     const uint8_t* __restrict__ blk,
+                                                     const int64_t* __restrict__ vis_off, VisGeom vg, int B,
+                                                     double* __restrict__ partials, int nparts) {
+  __shared__ double sred[8 * 2 * kMaxB];
+  const int l = blockIdx.y;
+  int64_t i = vis_off[l] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = i < vis_off[l + 1];
+  double v0 = 0.0, v1 = 0.0;
+  int b = 0;
+  if (valid) {
+    float2 u = degrid_one(grid + (size_t)l * vg.K1 * vg.K2, uv[i], vg);
+    float2 yy = y[i], vv = v[i], up = u_prev[i];
+    float2 z = make_float2(vv.x + 2.f * u.x - up.x, vv.y + 2.f * u.y - up.y);
+    float2 d = make_float2(z.x - yy.x, z.y - yy.y);
+    d_out[i] = d;
+    u_prev[i] = u;
+    b = blk[i];
+    v0 = (double)d.x * d.x + (double)d.y * d.y;
+    double rx = (double)yy.x - u.x, ry = (double)yy.y - u.y;
+    v1 = rx * rx + ry * ry;
+  }
+  block_partials<8>(v0, v1, b, valid, B, sred, partials + ((size_t)l * nparts + blockIdx.x) * 2 * B);
+}
+
+// Partial sums of ||z - y||^2 per block and d = z - y (standalone l2-ball projection).
+__global__ void __launch_bounds__(256) k_l2ball_partials(const float2* __restrict__ z, const float2* __restrict__ y,
+                                                         float2* __restrict__ d_out, const uint8_t* __restrict__ blk,
+                                                         const int64_t* __restrict__ vis_off, int B,
+                                                         double* __restrict__ partials, int nparts) {
+  __shared__ double sred[8 * 2 * kMaxB];
+  const int l = blockIdx.y;
+  int64_t i = vis_off[l] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = i < vis_off[l + 1];
+  double v0 = 0.0;
+  int b = 0;
+  if (valid) {
+    float2 zz = z[i], yy = y[i];
+    float2 d = make_float2(zz.x - yy.x, zz.y - yy.y);
+    d_out[i] = d;
+    b = blk[i];
+    v0 = (double)d.x * d.x + (double)d.y * d.y;
+  }
+  block_partials<8>(v0, 0.0, b, valid, B, sred, partials + ((size_t)l * nparts + blockIdx.x) * 2 * B);
+}
+
+// Per (channel, block): sum the CTA partials in order; scale = max(0, 1 - eps/||d||);
+// out[2][L*B] = (||d||, ||y - u||) in FP64.
+__global__ void k_block_finalize(const double* __restrict__ partials, int nparts, int B, int L,
+                                 const double* __restrict__ eps, float* __restrict__ scale, double* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L * B) return;
+  int l = k / B, b = k % B;
+  double s0 = 0.0, s1 = 0.0;
+  for (int p = 0; p < nparts; ++p) {
+    const double* pp = partials + ((size_t)l * nparts + p) * 2 * B;
+    s0 += pp[b];
+    s1 += pp[B + b];
+  }
+  double dn = sqrt(s0);
+  double e = eps ? eps[k] : 0.0;
+  if (scale) scale[k] = (float)(dn > e ? 1.0 - e / dn : 0.0);
+  if (out) {
+    out[k] = dn;
+    out[L * B + k] = sqrt(s1);
+  }
+}
+
+__global__ void k_l2ball_scale(const float2* __restrict__ d, const float* __restrict__ scale,
+                               const uint8_t* __restrict__ blk, const int64_t* __restrict__ vis_off, int B,
+                               float2* __restrict__ v) {
+  const int l = blockIdx.y;
+  int64_t i = vis_off[l] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= vis_off[l + 1]) return;
+  float s = scale[l * B + blk[i]];
+  float2 dd = d[i];
+  v[i] = make_float2(dd.x * s, dd.y * s);
+}
+
+// ----------------------------------------------------------- gridding G^T
+// One CTA per (64x64 tile, channel).  Pass (dr, dc) reads the visibilities of
+// source tile (tr - dr, tc - dc) whose footprint crosses into this tile and adds
+// only their taps in quadrant (dr, dc) of the source footprint, so each tap of
+// each visibility lands in exactly one (tile, pass).
+// Class order within a tile: 0 interior, 1 crosses down only, 2 crosses down
+// and right, 3 crosses right only.
+__global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
+                                              float2* __restrict__ v_write, const float2* __restrict__ uv,
+                                              const uint8_t* __restrict__ blk, const int32_t* __restrict__ tile_off,
+                                              const int64_t* __restrict__ vis_off, float2* __restrict__ grid,
+                                              VisGeom vg, int T, int ntr, int ntc, int B) {
+  extern __shared__ float sacc[];
+  float* are = sacc;
+  float* aim = sacc + T * T;
+  const int l = blockIdx.y;
+  const int tau = blockIdx.x;
+  const int tr = tau / ntc, tc = tau % ntc;
+  for (int k = threadIdx.x; k < 2 * T * T; k += blockDim.x) sacc[k] = 0.f;
+  __syncthreads();
+  const int64_t vbase = vis_off[l];
+  const int32_t* toff = tile_off + (size_t)l * (ntr * ntc * 4 + 1);
+  for (int pass = 0; pass < 4; ++pass) {
+    const int dr = pass >> 1, dc = pass & 1;
+    const int sr = (tr - dr + ntr) % ntr, sc = (tc - dc + ntc) % ntc;
+    const int sidx = (sr * ntc + sc) * 4;
+    int beg, end;
+    if (pass == 0) { beg = toff[sidx]; end = toff[sidx + 4]; }
+    else if (pass == 1) { beg = toff[sidx + 2]; end = toff[sidx + 4]; }   // crosses right: classes 2, 3
+    else if (pass == 2) { beg = toff[sidx + 1]; end = toff[sidx + 3]; }   // crosses down: classes 1, 2
+    else { beg = toff[sidx + 2]; end = toff[sidx + 3]; }                  // crosses both: class 2
+    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
+      const int64_t i = vbase + k;
+      float2 w = uv[i];
+      float2 val = vals[i];
+      if (blk_scale) {
+        float s = blk_scale[l * B + blk[i]];
+        val.x *= s;
+        val.y *= s;
+      }
+      if (pass == 0 && v_write) v_write[i] = val;
+      float wr[kTaps], wc[kTaps];
+      int kr = kb_weights(w.y, vg.tc.hi_r, vg.tc.lo_r, wr);
+      int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
+      int lr = (kr & (vg.K1 - 1)) - sr * T;   // start of the footprint in the source tile
+      int lc = (kc & (vg.K2 - 1)) - sc * T;
+#pragma unroll
+      for (int a = 0; a < kTaps; ++a) {
+        int rr = lr + a;
+        if ((rr >= T) != (dr == 1)) continue;
+        rr -= dr * T;
+        if (rr < 0 || rr >= T) continue;
+        float va = wr[a] * val.x, vb = wr[a] * val.y;
+#pragma unroll
+        for (int b = 0; b < kTaps; ++b) {
+          int cc = lc + b;
+          if ((cc >= T) != (dc == 1)) continue;
+          cc -= dc * T;
+          if (cc < 0 || cc >= T) continue;
+          atomicAdd(&are[rr * T + cc], wc[b] * va);
+          atomicAdd(&aim[rr * T + cc], wc[b] * vb);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
+  for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
+    int rr = k / T, cc = k % T;
+    int row = phys_row(tr * T + rr, vg.N1c, vg.N2c);
+    gl[(size_t)row * vg.K2 + tc * T + cc] = make_float2(are[k], aim[k]);
+  }
+}
+
+// ------------------------------------------------------------- launchers
+static VisGeom vis_geom(const Cube& cb) {
+  VisGeom vg;
+  vg.K1 = cb.K1; vg.K2 = cb.K2; vg.N1c = cb.N1c; vg.N2c = cb.N2c;
+  vg.tc = tap_const(cb.K1, cb.K2);
+  return vg;
+}
+
+int degrid_parts(const Cube& cb) { return (int)((cb.max_M + 255) / 256); }
+
+void launch_degrid(const Cube& cb, const float2* grid, float2* out, cudaStream_t st) {
+  dim3 grd(degrid_parts(cb), cb.L);
+  k_degrid<<<grd, 256, 0, st>>>(grid, cb.d_uv, out, cb.d_vis_off, vis_geom(cb));
+}
+
+void launch_degrid_pdfb(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
+                        float2* u_prev, double* partials, int nparts, cudaStream_t st) {
+  dim3 grd(nparts, cb.L);
+  k_degrid_pdfb<<<grd, 256, 0, st>>>(grid, cb.d_uv, y, v, d_out, u_prev, cb.d_blk, cb.d_vis_off, vis_geom(cb), cb.B,
+                                     partials, nparts);
+}
+
+void launch_l2ball_partials(const Cube& cb, const float2* z, const float2* y, float2* d, double* partials, int nparts,
+                            cudaStream_t st) {
+  dim3 grd(nparts, cb.L);
+  k_l2ball_partials<<<grd, 256, 0, st>>>(z, y, d, cb.d_blk, cb.d_vis_off, cb.B, partials, nparts);
+}
+
+void launch_block_finalize(const Cube& cb, const double* partials, int nparts, float* scale, double* out,
+                           cudaStream_t st) {
+  int n = cb.L * cb.B;
+  k_block_finalize<<<(n + 127) / 128, 128, 0, st>>>(partials, nparts, cb.B, cb.L, cb.d_eps, scale, out);
+}
+
+void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, float2* v, cudaStream_t st) {
+  dim3 grd(degrid_parts(cb), cb.L);
+  k_l2ball_scale<<<grd, 256, 0, st>>>(d, scale, cb.d_blk, cb.d_vis_off, cb.B, v);
+}
+
+void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write, float2* grid,
+                 cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024); attr = true; }
+  dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
+  size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(float);
+  k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
+                               vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
+}
+
+// ---------------------------------------------------- visibility reordering
+__global__ void k_vis_gather(const int64_t* __restrict__ perm, int64_t n, const float2* __restrict__ in,
+                             float2* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[perm[i]];
+}
+
+__global__ void k_vis_scatter(const int64_t* __restrict__ perm, int64_t n, const float2* __restrict__ in,
+                              float2* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[perm[i]] = in[i];
+}
+
+void launch_vis_gather(const int64_t* perm, int64_t n, const float2* in, float2* out, cudaStream_t st) {
+  if (n > 0) k_vis_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(perm, n, in, out);
+}
+
+void launch_vis_scatter(const int64_t* perm, int64_t n, const float2* in, float2* out, cudaStream_t st) {
+  if (n > 0) k_vis_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(perm, n, in, out);
+}
+
+void launch_measure(fhs_ctx* ctx, const Cube& cb, const float* x, float2* y, cudaStream_t st) {
+  launch_fft_forward(ctx, cb, x, ctx->s.grid, st);
+  launch_degrid(cb, ctx->s.grid, y, st);
+}
+
+// host-side replica of kb_weights' first-tap rule (exact same float operations)
+int host_first_tap(float om, int K) {
+  TapConst t = tap_const(K, K);
+  volatile float p = om * t.hi_r;
+  volatile float q = p - 3.5f;
+  return (int)floorf(q) + 1;
+}
+
+}  // namespace fhs

@@ -1,0 +1,266 @@
+"""Thin Python binding of the libfhs C ABI (include/fhs.h).
+
+Argument marshalling only: every operator runs in the CUDA kernels of
+libfhs.so.  Device arrays are torch tensors (float32 / complex64, contiguous,
+on the context's device); PyTorch provides memory and streams, nothing else.
+If libfhs.so is missing or cannot be loaded, every call raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfhs.so")
+
+FHS_WIN = {"triangular": 0, "sine": 1}
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "NONFINITE", 6: "UNSUPPORTED"}
+
+SYMBOLS = [
+    "fhs_create", "fhs_destroy", "fhs_get_sizes", "fhs_sync", "fhs_last_error", "fhs_vis_permutation",
+    "fhs_vis_to_internal", "fhs_vis_to_user", "fhs_measure", "fhs_adjoint", "fhs_opnorm_sq",
+    "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_prox_l21_sara_facets", "fhs_prox_nuclear_facets",
+    "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter",
+]
+
+
+class FhsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libfhs {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fhs_cube_desc(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("L", C.c_int32), ("Qy", C.c_int32), ("Qx", C.c_int32),
+                ("overlap", C.c_double), ("window", C.c_int32), ("B", C.c_int32),
+                ("M", C.POINTER(C.c_int64)), ("uv", C.POINTER(C.c_float)),
+                ("tau", C.c_double), ("zeta", C.c_double), ("kappa", C.c_double),
+                ("eta", C.POINTER(C.c_double)), ("mu", C.c_double),
+                ("mu_bar", C.POINTER(C.c_double)), ("eps", C.POINTER(C.c_double))]
+
+
+class fhs_sizes(C.Structure):
+    _fields_ = [("n_pix", C.c_int64), ("n_vis", C.c_int64), ("n_coef", C.c_int64), ("n_facet_pix", C.c_int64),
+                ("n_facets", C.c_int32), ("n_blocks", C.c_int32)]
+
+
+class fhs_state(C.Structure):
+    _fields_ = [("W", C.c_void_p), ("theta", C.c_void_p), ("P", C.c_void_p), ("theta_bar", C.c_void_p),
+                ("v", C.c_void_p), ("u_prev", C.c_void_p)]
+
+
+class fhs_iterate(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("Xcheck", C.c_void_p), ("y", C.c_void_p), ("state", fhs_state)]
+
+
+class fhs_iter_stats(C.Structure):
+    _fields_ = [("xi", C.c_double), ("res_norm", C.c_double), ("eps_norm", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfhs.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FhsError(2, f"{path} not found: build it with __graft_entry__.build() (CUDA toolkit required)")
+    lib = C.CDLL(path)
+    vp, i32, i64p, dp = C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    sig = {
+        "fhs_create": ([C.POINTER(fhs_cube_desc), i32, vp, C.POINTER(vp)], i32),
+        "fhs_destroy": ([vp], i32),
+        "fhs_get_sizes": ([vp, i32, C.POINTER(fhs_sizes)], i32),
+        "fhs_sync": ([vp], i32),
+        "fhs_last_error": ([vp], C.c_char_p),
+        "fhs_vis_permutation": ([vp, i32, i64p], i32),
+        "fhs_vis_to_internal": ([vp, i32, vp, vp], i32),
+        "fhs_vis_to_user": ([vp, i32, vp, vp], i32),
+        "fhs_measure": ([vp, i32, vp, vp], i32),
+        "fhs_adjoint": ([vp, i32, vp, vp], i32),
+        "fhs_opnorm_sq": ([vp, i32, i32, C.c_double, dp], i32),
+        "fhs_sara_analysis": ([vp, i32, vp, vp], i32),
+        "fhs_sara_synthesis": ([vp, i32, vp, vp], i32),
+        "fhs_prox_l21_sara_facets": ([vp, i32, vp, vp, vp, vp], i32),
+        "fhs_prox_nuclear_facets": ([vp, i32, vp, vp, vp, vp], i32),
+        "fhs_proj_l2ball_blocks": ([vp, i32, vp, vp, vp, dp], i32),
+        "fhs_reweight": ([vp, i32, vp, vp, vp], i32),
+        "fhs_pdfb_iter": ([vp, C.POINTER(fhs_iterate), i32, C.POINTER(fhs_iter_stats)], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("libfhs takes contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+@dataclass
+class CubeParams:
+    """One spectral sub-cube for fhs_create (host arrays, float64 parameters)."""
+    n1: int
+    n2: int
+    L: int
+    Qy: int
+    Qx: int
+    overlap: float
+    window: str
+    M_lb: np.ndarray          # [L][B] int64
+    uv: np.ndarray            # [sum M][2] float32, channel-major, block-contiguous
+    eta: np.ndarray           # [L]
+    mu: float
+    mu_bar: np.ndarray        # [Qy*Qx]
+    eps: np.ndarray           # [L][B]
+    tau: float = 0.33
+    zeta: float = 1.0
+    kappa: float = 1.0
+
+
+class Context:
+    """Owns an fhs_ctx; methods mirror the C-ABI calls one to one."""
+
+    def __init__(self, cubes: list[CubeParams], stream=None):
+        import torch
+        self.lib = load()
+        self._keep = []
+        descs = (fhs_cube_desc * len(cubes))()
+        for d, cp in zip(descs, cubes):
+            M = np.ascontiguousarray(cp.M_lb, dtype=np.int64).ravel()
+            uv = np.ascontiguousarray(cp.uv, dtype=np.float32).ravel()
+            eta = np.ascontiguousarray(cp.eta, dtype=np.float64).ravel()
+            mub = np.ascontiguousarray(cp.mu_bar, dtype=np.float64).ravel()
+            eps = np.ascontiguousarray(cp.eps, dtype=np.float64).ravel()
+            self._keep += [M, uv, eta, mub, eps]
+            d.n1, d.n2, d.L, d.Qy, d.Qx = cp.n1, cp.n2, cp.L, cp.Qy, cp.Qx
+            d.overlap, d.window, d.B = cp.overlap, FHS_WIN[cp.window], int(np.asarray(cp.M_lb).shape[1])
+            d.M = M.ctypes.data_as(C.POINTER(C.c_int64))
+            d.uv = uv.ctypes.data_as(C.POINTER(C.c_float))
+            d.tau, d.zeta, d.kappa, d.mu = cp.tau, cp.zeta, cp.kappa, cp.mu
+            d.eta = eta.ctypes.data_as(C.POINTER(C.c_double))
+            d.mu_bar = mub.ctypes.data_as(C.POINTER(C.c_double))
+            d.eps = eps.ctypes.data_as(C.POINTER(C.c_double))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
+        h = C.c_void_p()
+        st = self.lib.fhs_create(descs, len(cubes), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise FhsError(st, self.lib.fhs_last_error(None).decode())
+        self.h = h
+        self.cubes = cubes
+        self._keep = []
+
+    # ---------------------------------------------------------------- utils
+    def _check(self, st):
+        if st != 0:
+            raise FhsError(st, self.lib.fhs_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fhs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sizes(self, cube: int = 0) -> dict:
+        s = fhs_sizes()
+        self._check(self.lib.fhs_get_sizes(self.h, cube, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in fhs_sizes._fields_}
+
+    def sync(self):
+        self._check(self.lib.fhs_sync(self.h))
+
+    def fhs_vis_permutation(self, cube: int = 0) -> np.ndarray:
+        n = self.sizes(cube)["n_vis"]
+        out = np.zeros(n, dtype=np.int64)
+        self._check(self.lib.fhs_vis_permutation(self.h, cube, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def fhs_vis_to_internal(self, cube, user, internal):
+        self._check(self.lib.fhs_vis_to_internal(self.h, cube, _ptr(user), _ptr(internal)))
+
+    def fhs_vis_to_user(self, cube, internal, user):
+        self._check(self.lib.fhs_vis_to_user(self.h, cube, _ptr(internal), _ptr(user)))
+
+    # ------------------------------------------------------------ operators
+    def fhs_measure(self, cube, x, y):
+        self._check(self.lib.fhs_measure(self.h, cube, _ptr(x), _ptr(y)))
+
+    def fhs_adjoint(self, cube, v, x):
+        self._check(self.lib.fhs_adjoint(self.h, cube, _ptr(v), _ptr(x)))
+
+    def fhs_opnorm_sq(self, cube, max_iter=100, rel_tol=1e-4) -> np.ndarray:
+        L = self.cubes[cube].L
+        out = np.zeros(L, dtype=np.float64)
+        self._check(self.lib.fhs_opnorm_sq(self.h, cube, max_iter, rel_tol,
+                                           out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def fhs_sara_analysis(self, cube, x, coef):
+        self._check(self.lib.fhs_sara_analysis(self.h, cube, _ptr(x), _ptr(coef)))
+
+    def fhs_sara_synthesis(self, cube, coef, x):
+        self._check(self.lib.fhs_sara_synthesis(self.h, cube, _ptr(coef), _ptr(x)))
+
+    def fhs_prox_l21_sara_facets(self, cube, xcheck, W, theta, A):
+        self._check(self.lib.fhs_prox_l21_sara_facets(self.h, cube, _ptr(xcheck), _ptr(W), _ptr(theta), _ptr(A)))
+
+    def fhs_prox_nuclear_facets(self, cube, xcheck, P, theta_bar, A):
+        self._check(self.lib.fhs_prox_nuclear_facets(self.h, cube, _ptr(xcheck), _ptr(P), _ptr(theta_bar), _ptr(A)))
+
+    def fhs_proj_l2ball_blocks(self, cube, z, y, v_out, want_norms=True):
+        nb = self.sizes(cube)["n_blocks"]
+        out = np.zeros(nb, dtype=np.float64) if want_norms else None
+        self._check(self.lib.fhs_proj_l2ball_blocks(
+            self.h, cube, _ptr(z), _ptr(y), _ptr(v_out),
+            out.ctypes.data_as(C.POINTER(C.c_double)) if want_norms else None))
+        return out
+
+    def fhs_reweight(self, cube, x, theta, theta_bar):
+        self._check(self.lib.fhs_reweight(self.h, cube, _ptr(x), _ptr(theta), _ptr(theta_bar)))
+
+    def fhs_pdfb_iter(self, iterates: list[dict], n_iter: int, want_stats: bool = True):
+        arr = (fhs_iterate * len(iterates))()
+        for a, it in zip(arr, iterates):
+            a.X, a.Xcheck, a.y = _ptr(it["X"]), _ptr(it["Xcheck"]), _ptr(it["y"])
+            s = it["state"]
+            a.state.W, a.state.theta, a.state.P = _ptr(s["W"]), _ptr(s["theta"]), _ptr(s["P"])
+            a.state.theta_bar, a.state.v, a.state.u_prev = _ptr(s["theta_bar"]), _ptr(s["v"]), _ptr(s["u_prev"])
+        stats = (fhs_iter_stats * len(iterates))() if want_stats else None
+        self._check(self.lib.fhs_pdfb_iter(self.h, arr, n_iter, stats))
+        if not want_stats:
+            return None
+        return [{"xi": s.xi, "res_norm": s.res_norm, "eps_norm": s.eps_norm} for s in stats]
+
+    # ------------------------------------------------------------ helpers
+    def new_state(self, cube: int = 0) -> dict:
+        """Zero duals and unit weights (Algorithm 1 starts from X = 0, weights 1)."""
+        import torch
+        sz = self.sizes(cube)
+        L = self.cubes[cube].L
+        dev = self.device
+        return {
+            "W": torch.zeros(L * sz["n_coef"], device=dev),
+            "theta": torch.ones(sz["n_coef"], device=dev),
+            "P": torch.zeros(L * sz["n_facet_pix"], device=dev),
+            "theta_bar": torch.ones(sz["n_facets"] * L, device=dev),
+            "v": torch.zeros(sz["n_vis"], dtype=torch.complex64, device=dev),
+            "u_prev": torch.zeros(sz["n_vis"], dtype=torch.complex64, device=dev),
+        }
