@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""PDFB iterations per second of the Faceted HyperSARA hot path on GB300.
+
+Workload (default "large"): 4096 x 4096 image, 64 channels as 4 channel-
+interleaved sub-cubes of 16, 16 x 16 spatial facets (10 % nuclear overlap),
+M = 0.5 N = 8,388,608 visibilities per channel in 8 uv-radial blocks, iSNR
+30 dB; synthetic sky (Gaussian blobs + point sources with curved power-law
+spectra) and Gaussian uv coverage scaled with frequency.  One step = one
+iteration of Algorithm 2 on all 4 sub-cubes.  Inputs are resident in HBM
+(working set ~100 GB, far above the 129 MB L2, so no flush is needed).
+
+--impl reference times the FP64 oracle (test infrastructure) on the host
+cores on a bounded sample of the same workload, scaled to one iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fhs_synth as fs  # noqa: E402
+
+METRIC = "PDFB iter/s at 4096^2 x 64ch"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="large", choices=list(fs.WORKLOADS))
+    ap.add_argument("--opnorm-iters", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ops", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- workload
+def chi_mean_std(k: int):
+    m = math.sqrt(2.0) * math.exp(math.lgamma((k + 1) / 2.0) - math.lgamma(k / 2.0))
+    return m, math.sqrt(max(k - m * m, 0.0))
+
+
+def facet_pixels(n: int, Q: int, rho: float) -> list[int]:
+    tb = [(i * n) // Q for i in range(Q + 1)]
+    side = [(tb[i + 1] - tb[i]) + (0 if i == 0 else int(math.floor(rho * (tb[i + 1] - tb[i])))) for i in range(Q)]
+    return [a * b for a in side for b in side]
+
+
+def setup(spec: fs.CubeSpec, torch, seed_offset: int, opnorm_iters: int, log):
+    """Create the context, the data y = Phi x + noise, the parameters and the state of every sub-cube."""
+    from paper_2003_07358_gb300.fhs import Context, CubeParams
+    rng = np.random.default_rng(spec.seed + seed_offset)
+    sources = fs.sky_sources(spec, rng)
+    base = fs.base_uv(spec, rng)
+    blocks = fs.radial_blocks(base, spec.B)
+    perm = np.concatenate(blocks)
+    Lc, n, Q = spec.Lc, spec.n, spec.Q
+    M_lb = np.array([[b.size for b in blocks]] * Lc, dtype=np.int64)
+    cubes = []
+    t0 = time.time()
+    for c in range(spec.C):
+        chans = fs.subcube_channels(spec, c)
+        uv = np.concatenate([fs.channel_uv(base, spec, l)[perm] for l in chans])
+        cubes.append(CubeParams(n1=n, n2=n, L=Lc, Qy=Q, Qx=Q, overlap=spec.overlap, window=spec.window, M_lb=M_lb,
+                                uv=uv, eta=np.ones(Lc), mu=0.0, mu_bar=np.zeros(Q * Q), eps=np.zeros((Lc, spec.B))))
+    ctx = Context(cubes)
+    del cubes
+    log(f"context created in {time.time() - t0:.1f} s")
+    dev = ctx.device
+    iterates = []
+    npix = facet_pixels(n, Q, spec.overlap)
+    gen = torch.Generator(device=dev)
+    for c in range(spec.C):
+        chans = fs.subcube_channels(spec, c)
+        sz = ctx.sizes(c)
+        x = torch.empty((Lc, n, n), device=dev)
+        for i, l in enumerate(chans):
+            x[i].copy_(torch.from_numpy(fs.render_channel(spec, sources, int(l)).astype(np.float32)))
+        y = torch.empty(sz["n_vis"], dtype=torch.complex64, device=dev)
+        ctx.fhs_measure(c, x, y)
+        del x
+        zero = torch.zeros_like(y)
+        tmp = torch.empty_like(y)
+        dn = ctx.fhs_proj_l2ball_blocks(c, y, zero, tmp).reshape(Lc, spec.B)
+        del zero, tmp
+        Ml = M_lb.sum(axis=1)
+        sigma = np.sqrt((dn ** 2).sum(axis=1)) / np.sqrt(Ml) * 10 ** (-spec.isnr_db / 20)
+        gen.manual_seed(spec.seed * 100 + seed_offset * 10 + c)
+        off = 0
+        for i in range(Lc):
+            m = int(Ml[i])
+            noise = torch.randn(m, dtype=torch.complex64, device=dev, generator=gen)
+            y[off:off + m] += float(sigma[i]) * noise
+            off += m
+        e2 = sigma ** 2 * (Ml + 2 * np.sqrt(Ml))
+        eps = np.sqrt(e2[:, None] * M_lb / Ml[:, None])
+        opn = ctx.fhs_opnorm_sq(c, opnorm_iters, 1e-4)
+        sb = sigma / np.sqrt(opn)
+        sbar = math.sqrt(float(np.mean(sb ** 2)))
+        m_, s_ = chi_mean_std(Lc)
+        mu = sbar * (m_ + s_)
+        mu_bar = np.array([sbar * math.sqrt(p * Lc / min(p, Lc)) for p in npix])
+        ctx.fhs_set_params(c, 0.33, 1.0, 1.0, 1.0 / opn, mu, mu_bar, eps)
+        X = torch.zeros((Lc, n, n), device=dev)
+        iterates.append({"X": X, "Xcheck": torch.zeros_like(X), "y": y, "state": ctx.new_state(c)})
+    ctx.sync()
+    log(f"data, parameters and state ready in {time.time() - t0:.1f} s")
+    return ctx, iterates
+
+
+# ------------------------------------------------------- algorithmic bytes
+def op_bytes(spec: fs.CubeSpec, n_coef: int, n_facet_pix: int) -> dict:
+    """Algorithmic HBM bytes per sub-cube of each operator (each array read or
+    written once, pruned FFT passes, FP32 / complex64)."""
+    N = spec.n * spec.n
+    L = spec.Lc
+    M = spec.M
+    return {
+        "sara": 4 * N * L + 8 * n_coef * L + 4 * n_coef + 4 * N * L,
+        "nuclear": 12 * n_facet_pix * L + 8 * N * L + 4 * N * L,
+        "data": L * (200 * N + 32 * M),          # measure + adjoint
+        "primal": 24 * N * L,
+    }
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_iteration_estimate(spec: fs.CubeSpec, budget_scale: float = 1.0) -> dict:
+    """Seconds of one oracle iteration of the workload, from timed samples of
+    each operator scaled by the number of units per iteration."""
+    from oracle import nufft as nu
+    from oracle import prox as px
+    from oracle import wavelets as wv
+    rng = np.random.default_rng(11)
+    n, Lc, C, Q = spec.n, spec.Lc, spec.C, spec.Q
+    L = spec.L
+    out = {}
+    # data term: forward FFT of one channel + degrid / grid of a visibility sample
+    x = rng.random((n, n))
+    t = time.perf_counter()
+    g = nu.zpad_fft(x)
+    t_fft = time.perf_counter() - t
+    ms = max(2000, int(20000 * budget_scale))
+    uv = rng.uniform(-math.pi / 2, math.pi / 2, (ms, 2))
+    t = time.perf_counter()
+    y = nu.degrid(g, uv)
+    t_deg = time.perf_counter() - t
+    t = time.perf_counter()
+    nu.grid_adjoint(y, uv, 2 * n, 2 * n)
+    t_grd = time.perf_counter() - t
+    per_ch = 2 * t_fft + (t_deg + t_grd) * spec.M / ms
+    out["data"] = per_ch * L
+    # SARA: analysis + synthesis of a crop, scaled by area and channels
+    s = min(n, 512 if budget_scale >= 1 else 256)
+    xs = rng.random((1, s, s))
+    t = time.perf_counter()
+    cf = wv.sara_analysis(xs)
+    wv.sara_synthesis(cf, s, s)
+    out["sara"] = (time.perf_counter() - t) * (n * n) / (s * s) * L
+    # nuclear: Jacobi SVD of one facet-sized matrix, scaled by facets and sub-cubes
+    side = n // Q + int(math.floor(spec.overlap * n / Q))
+    rows = min(side * side, 8192 if budget_scale >= 1 else 4096)
+    Z = rng.standard_normal((rows, Lc))
+    t = time.perf_counter()
+    px.jacobi_svd(Z)
+    out["nuclear"] = (time.perf_counter() - t) * (side * side / rows) * Q * Q * C
+    # primal: elementwise update of one channel
+    X = rng.random((n, n))
+    A = rng.random((n, n))
+    t = time.perf_counter()
+    Xn = px.proj_nonneg_real(X - 0.33 * A)
+    _ = 2 * Xn - X
+    out["primal"] = (time.perf_counter() - t) * L
+    out["total"] = sum(out.values())
+    return out
+
+
+def run_reference(args, spec):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_iteration_estimate(spec, 0.25)
+    vals = []
+    t0 = time.time()
+    for _ in range(args.steps):
+        est = oracle_iteration_estimate(spec, 0.25)
+        vals.append(1.0 / est["total"])
+    wall = time.time() - t0
+    v = statistics.median(vals)
+    sample = ("per step: one channel's 2n x 2n FFT, 5000 degrid + grid visibilities, SARA on a 256^2 crop, "
+              "Jacobi SVD of a 4096 x 16 facet slice, one channel's primal update; each scaled to the "
+              "units of one full iteration")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec.name, "oracle": "numpy float64"},
+            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- main
+def main():
+    args = parse()
+    spec = fs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, spec)
+        return
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    def log(msg):
+        if rank == 0:
+            print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    ctx, its = setup(spec, torch, rank, args.opnorm_iters, log)
+    stream = ctx.stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ctx.fhs_pdfb_iter(its, 1, want_stats=False)
+    st = ctx.fhs_pdfb_iter(its, 1, want_stats=True)
+    log(f"warm-up done, stats {st}")
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = ctx.fhs_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.fhs_pdfb_iter(its, 1, want_stats=False)
+    e1.record(stream)
+    barrier()
+    launches = ctx.fhs_kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+    log(f"{ms:.1f} ms per iteration")
+
+    # per-operator times through their own C-ABI calls (same stream, CUDA events)
+    hbm, peak_kind = peaks()
+    ops = {}
+    sz = ctx.sizes(0)
+    if not args.no_ops:
+        A = torch.zeros_like(its[0]["X"])
+        ybuf = torch.empty_like(its[0]["y"])
+
+        def time_op(fn, reps=3):
+            fn()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps / 1000.0
+
+        it0 = its[0]
+        s0 = it0["state"]
+        times = {
+            "sara": time_op(lambda: ctx.fhs_prox_l21_sara_facets(0, it0["Xcheck"], s0["W"], s0["theta"], A)),
+            "nuclear": time_op(lambda: ctx.fhs_prox_nuclear_facets(0, it0["Xcheck"], s0["P"], s0["theta_bar"], A)),
+            "data": time_op(lambda: (ctx.fhs_measure(0, it0["X"], ybuf), ctx.fhs_adjoint(0, ybuf, A))),
+        }
+        byts = op_bytes(spec, sz["n_coef"], sz["n_facet_pix"])
+        for k, t in times.items():
+            gbs = byts[k] / t / 1e9
+            ops[k] = {"ms_per_subcube": round(t * 1e3, 3), "algorithmic_GB": round(byts[k] / 1e9, 3),
+                      "GB_s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 4)}
+        ops["primal"] = {"algorithmic_GB": round(byts["primal"] / 1e9, 3)}
+        del A, ybuf
+    dominant = max((k for k in ops if "ms_per_subcube" in ops[k]), key=lambda k: ops[k]["ms_per_subcube"],
+                   default=None)
+    roofline = None
+    if dominant:
+        d = ops[dominant]
+        roofline = {"bound": "hbm", "kernel": dominant, "achieved": d["GB_s"], "peak": hbm, "unit": "GB/s",
+                    "frac": d["frac_of_hbm"], "traffic": None, "peak_kind": peak_kind}
+
+    # end to end through the C ABI with host buffers: H2D of y, one iteration, D2H of the statistics
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.empty(it["y"].shape, dtype=it["y"].dtype, pin_memory=True) for it in its]
+        for h, it in zip(hosts, its):
+            h.copy_(it["y"])
+        h2d = sum(h.numel() * 8 for h in hosts)
+        d2h = len(its) * (2 * 1216 * 8 + 2 * spec.Lc * spec.B * 8)
+        k = max(2, args.steps // 2)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            for h, it in zip(hosts, its):
+                it["y"].copy_(h, non_blocking=True)
+            ctx.fhs_pdfb_iter(its, 1, want_stats=True)
+        b.record(stream)
+        barrier()
+        ems = a.elapsed_time(b) / k
+        e2e = {"value": world * 1000.0 / ems, "unit": "iter/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+        del hosts
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = time.time()
+        est = oracle_iteration_estimate(spec, 1.0)
+        cpu = {"value": 1.0 / est["total"], "unit": "iter/s", "cores": 1, "kind": "oracle",
+               "sample": ("one channel's 2n x 2n FFT, 20000 degrid + grid visibilities, SARA on a 512^2 crop, "
+                          "Jacobi SVD of an 8192 x 16 facet slice, one channel's primal update, each scaled "
+                          "to the units of one full iteration; seconds per iteration by operator: "
+                          + ", ".join(f"{k} {v:.0f}" for k, v in est.items())),
+               "wall_s": round(time.time() - t, 1)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": spec.name, "n": spec.n, "L": spec.L, "subcubes": spec.C,
+                           "facets": f"{spec.Q}x{spec.Q}", "vis_per_channel": spec.M, "blocks": spec.B,
+                           "path": "FP32 (plain kernels, FP64 reductions)",
+                           "l2": "working set ~100 GB >> 129 MB L2; no flush"},
+                "roofline": roofline, "operators": ops, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

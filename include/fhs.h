@@ -192,6 +192,15 @@ fhs_status fhs_proj_l2ball_blocks(fhs_ctx* ctx, int32_t cube, const float* z, co
  * (Eq. 10) and theta_bar_{q,j} = mu_bar_q / (s_j(D_q S~_q x) + mu_bar_q) (Eq. 9). */
 fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta, float* theta_bar);
 
+/* Replace the algorithm parameters of a cube (same meaning and host arrays as in
+ * fhs_cube_desc: eta [L], mu_bar [Qy*Qx], eps [L*B]).  Lets a caller compute
+ * eta = 1/||Phi_l||^2 with fhs_opnorm_sq and the noise-based heuristics
+ * (Sections 2.3-2.4) on a context before iterating.  Synchronising. */
+fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, double kappa, const double* eta,
+                          double mu, const double* mu_bar, const double* eps);
+/* Number of CUDA kernels this library has launched in this process so far. */
+uint64_t fhs_kernel_launches(void);
+
 /* n_iter iterations of Algorithm 2 on every cube.  it: host [ncubes].
  * stats: host [ncubes] or NULL; when not NULL the call synchronises and
  * fills the statistics of the last iteration. */

@@ -85,7 +85,7 @@ struct Scratch {
   float2* vis = nullptr;     size_t vis_elems = 0;      // [n_vis]
   double* red = nullptr;     size_t red_elems = 0;      // reduction partials
   double* red_host = nullptr;                           // pinned host copy
-  float* gram = nullptr;     size_t gram_elems = 0;     // nuclear Gram partials
+  double* gram = nullptr;    size_t gram_elems = 0;     // nuclear Gram partials (FP64)
   float* nucM = nullptr;     size_t nucM_elems = 0;     // [Q][L][L]
   float* blk_scale = nullptr;                           // [L*B]
   double* blk_out = nullptr;                            // [2][L*B]
@@ -104,6 +104,9 @@ struct fhs_ctx {
 };
 
 namespace fhs {
+
+// Count of kernel launches made by this library (fhs_kernel_launches).
+void note_launches(int n);
 
 // --------------------------------------------------------- kernel launchers
 // Tables (constant memory lives in the translation unit that uses it).

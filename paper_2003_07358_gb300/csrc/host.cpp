@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <complex>
 #include <string>
 #include <vector>
@@ -15,6 +16,12 @@
 
 using namespace fhs;
 using cd = std::complex<double>;
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+
+void fhs::note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -488,7 +495,7 @@ void alloc_scratch(fhs_ctx* ctx) {
   s.vis = dalloc<float2>(vis); s.vis_elems = vis;
   s.red = dalloc<double>(red); s.red_elems = red;
   FHS_CUDA(cudaMallocHost((void**)&s.red_host, red * sizeof(double)));
-  s.gram = dalloc<float>(gram); s.gram_elems = gram;
+  s.gram = dalloc<double>(gram); s.gram_elems = gram;
   s.nucM = dalloc<float>(nm); s.nucM_elems = nm;
   s.blk_scale = dalloc<float>(lb);
   s.blk_out = dalloc<double>(2 * lb + 2 * kMaxL);
@@ -656,12 +663,22 @@ fhs_status fhs_opnorm_sq(fhs_ctx* ctx, int32_t cube, int32_t max_iter, double re
     const int L = cb.L;
     const int64_t N = (int64_t)cb.n1 * cb.n2;
     const int np = 64;
-    std::vector<float> ones(N, (float)(1.0 / sqrt((double)N)));
-    for (int l = 0; l < L; ++l) upload(ctx->s.img2 + l * N, ones.data(), N, st);
+    // deterministic pseudo-random start (xorshift64), unit norm per channel: a
+    // constant start is an even image and stays in the even eigenspace of the
+    // point-symmetric operator Re(Phi^dagger Phi)
+    std::vector<float> x0(N);
+    uint64_t state = 0x9E3779B97F4A7C15ull;
+    double nrm = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+      state ^= state << 13; state ^= state >> 7; state ^= state << 17;
+      x0[i] = (float)((double)(state >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+      nrm += (double)x0[i] * x0[i];
+    }
+    for (int64_t i = 0; i < N; ++i) x0[i] = (float)(x0[i] / sqrt(nrm));
+    for (int l = 0; l < L; ++l) upload(ctx->s.img2 + l * N, x0.data(), N, st);
     std::vector<double> val(L, 0.0), inv(L);
     std::vector<char> done(L, 0);
-    double* dinv = ctx->s.blk_out + 2 * ctx->s.vis_elems * 0;   // reuse: first L doubles of blk_out tail
-    dinv = ctx->s.blk_out;
+    double* dinv = ctx->s.blk_out;   // L doubles of scratch
     for (int it = 0; it < max_iter; ++it) {
       launch_measure(ctx, cb, ctx->s.img2, ctx->s.vis, st);
       adjoint_into(ctx, cb, ctx->s.vis, nullptr, nullptr, ctx->s.img, nullptr, false);
@@ -761,6 +778,34 @@ fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta
     check_launch("reweight");
   });
 }
+
+fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, double kappa, const double* eta,
+                          double mu, const double* mu_bar, const double* eps) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(eta && mu_bar && eps, FHS_ERR_INVALID_ARG, "NULL parameter array");
+    FHS_REQUIRE(cube >= 0 && cube < (int32_t)ctx->cubes.size(), FHS_ERR_INVALID_ARG, "cube index out of range");
+    Cube& cb = ctx->cubes[cube];
+    FHS_REQUIRE(std::isfinite(tau) && std::isfinite(zeta) && std::isfinite(kappa) && std::isfinite(mu) && tau > 0 &&
+                    zeta > 0 && kappa > 0 && mu >= 0,
+                FHS_ERR_INVALID_ARG, "tau, zeta, kappa must be positive and mu non-negative");
+    const int Q = cb.Qy * cb.Qx;
+    for (int l = 0; l < cb.L; ++l) FHS_REQUIRE(std::isfinite(eta[l]) && eta[l] > 0, FHS_ERR_INVALID_ARG, "bad eta");
+    for (int q = 0; q < Q; ++q) FHS_REQUIRE(std::isfinite(mu_bar[q]) && mu_bar[q] >= 0, FHS_ERR_INVALID_ARG, "bad mu_bar");
+    for (int k = 0; k < cb.L * cb.B; ++k) FHS_REQUIRE(std::isfinite(eps[k]) && eps[k] >= 0, FHS_ERR_INVALID_ARG, "bad eps");
+    cb.tau = tau; cb.zeta = zeta; cb.kappa = kappa; cb.mu = mu;
+    cb.eta.assign(eta, eta + cb.L);
+    cb.mu_bar.assign(mu_bar, mu_bar + Q);
+    cb.eps.assign(eps, eps + cb.L * cb.B);
+    std::vector<float> eta_f(cb.eta.begin(), cb.eta.end()), mub_f(cb.mu_bar.begin(), cb.mu_bar.end());
+    FHS_CUDA(cudaStreamSynchronize(ctx->stream));
+    upload(cb.d_eps, cb.eps.data(), cb.eps.size(), ctx->stream);
+    upload(cb.d_eta, eta_f.data(), eta_f.size(), ctx->stream);
+    upload(cb.d_mubar, mub_f.data(), mub_f.size(), ctx->stream);
+    FHS_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+uint64_t fhs_kernel_launches(void) { return g_launches.load(); }
 
 fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fhs_iter_stats* stats) {
   return guarded(ctx, [&] {

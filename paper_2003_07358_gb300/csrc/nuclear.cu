@@ -23,12 +23,24 @@ __device__ __forceinline__ float facet_weight(const NucFacet& f, const float* __
   return win[f.wy_off + rr] * win[f.wx_off + cc];
 }
 
-// Partial Gram of chunk blockIdx.x of facet blockIdx.y.  Thread owns an
-// LB x LB block of G; Lp = L rounded up to a multiple of LB.
+// Error-free transformation a + b = s + e (Knuth TwoSum), no contraction.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Partial Gram of chunk blockIdx.x of facet blockIdx.y, accumulated in
+// float-float: each product a*b = p + e exactly (FMA), the running sum keeps a
+// high part and a compensation term, so the partial equals the exact Gram of
+// the FP32 matrix Z to ~1e-14 relative.  (A plain FP32 Gram has absolute
+// errors ~eps * lambda_max, which wipes out singular values below
+// sqrt(eps) s_max.)  Thread owns an LB x LB block of G; Lp = L rounded up to a
+// multiple of LB.  Output: FP64 partials [Q][nchunk_max][L][L].
 template <int LB>
 __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, const float* __restrict__ P,
                                               const NucFacet* __restrict__ facets, const float* __restrict__ win,
-                                              int n1, int n2, int L, int use_P, float* __restrict__ part,
+                                              int n1, int n2, int L, int use_P, double* __restrict__ part,
                                               int nchunk_max) {
   __shared__ float z[kGramSub][kMaxL + 1];
   const int q = blockIdx.y;
@@ -41,12 +53,12 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
   const int Lp = (L + LB - 1) / LB * LB;
   const int nb = Lp / LB;
   const int ta = threadIdx.x / nb, tb = threadIdx.x % nb;
-  const bool active = ta < nb;
-  float acc[LB][LB];
+  const bool active = ta < nb && ta <= tb;
+  float hi[LB][LB], lo[LB][LB];
 #pragma unroll
   for (int i = 0; i < LB; ++i)
 #pragma unroll
-    for (int j = 0; j < LB; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < LB; ++j) hi[i][j] = lo[i][j] = 0.f;
   const size_t N = (size_t)n1 * n2;
   for (int s0 = p0; s0 < p1; s0 += kGramSub) {
     for (int idx = threadIdx.x; idx < kGramSub * Lp; idx += blockDim.x) {
@@ -72,19 +84,30 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
 #pragma unroll
         for (int i = 0; i < LB; ++i)
 #pragma unroll
-          for (int j = 0; j < LB; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < LB; ++j) {
+            float pr = __fmul_rn(a[i], b[j]);
+            float pe = __fmaf_rn(a[i], b[j], -pr);
+            float s, e;
+            two_sum(hi[i][j], pr, s, e);
+            hi[i][j] = s;
+            lo[i][j] = __fadd_rn(lo[i][j], __fadd_rn(e, pe));
+          }
       }
     }
     __syncthreads();
   }
   if (active) {
-    float* out = part + ((size_t)q * nchunk_max + blockIdx.x) * L * L;
+    double* out = part + ((size_t)q * nchunk_max + blockIdx.x) * L * L;
 #pragma unroll
     for (int i = 0; i < LB; ++i)
 #pragma unroll
       for (int j = 0; j < LB; ++j) {
         int a = ta * LB + i, b = tb * LB + j;
-        if (a < L && b < L) out[a * L + b] = acc[i][j];
+        double v = (double)hi[i][j] + (double)lo[i][j];
+        if (a < L && b < L) {
+          out[a * L + b] = v;
+          out[b * L + a] = v;
+        }
       }
   }
 }
@@ -94,7 +117,7 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
 // sorted descending, then either M = V diag(m) V^T with
 // m_j = min(1, alpha_j / s_j), alpha_j = (mu_bar_q / zeta) theta_bar_q[rank j]
 // (dual mode), or theta_bar_q[rank] = mu_bar_q / (s + mu_bar_q) (weights mode).
-__global__ void __launch_bounds__(32) k_eig(const float* __restrict__ part, int nchunk_max,
+__global__ void __launch_bounds__(32) k_eig(const double* __restrict__ part, int nchunk_max,
                                             const NucFacet* __restrict__ facets, int L,
                                             const float* __restrict__ theta_bar, const float* __restrict__ mubar,
                                             float inv_zeta, float* __restrict__ Mout, float* __restrict__ tb_out,
@@ -111,7 +134,7 @@ __global__ void __launch_bounds__(32) k_eig(const float* __restrict__ part, int 
   const int nch = (Nq + kGramChunk - 1) / kGramChunk;
   for (int idx = lane; idx < L * L; idx += 32) {
     double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += (double)part[((size_t)q * nchunk_max + c) * L * L + idx];
+    for (int c = 0; c < nch; ++c) s += part[((size_t)q * nchunk_max + c) * L * L + idx];
     int a = idx / L, b = idx % L;
     G[a * Ls + b] = s;
     V[a * Ls + b] = (a == b) ? 1.0 : 0.0;
@@ -266,11 +289,13 @@ void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P,
   if (L <= 16) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   else if (L <= 32) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   else k_gram<4><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  note_launches(1);
   size_t sm = (size_t)2 * L * (L + 1) * sizeof(double) + L * sizeof(double) + L * sizeof(int);
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024); attr = true; }
   k_eig<<<Q, 32, sm, st>>>(ctx->s.gram, nch, cb.d_facets, L, theta_bar, cb.d_mubar, (float)(1.0 / cb.zeta),
                            ctx->s.nucM, theta_bar_out, weights_mode ? 1 : 0, 40);
+  note_launches(1);
   if (weights_mode) return;
   dim3 ga((cb.n2 + 31) / 32, (cb.n1 + 7) / 8);
   const int* tyo = cb.d_tile_of;
@@ -279,6 +304,7 @@ void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P,
   if (L <= 16) k_apply<16><<<ga, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, ctx->s.nucM, cb.n1, cb.n2, L, cb.Qy, cb.Qx, tyo, txo, zeta, A);
   else if (L <= 32) k_apply<32><<<ga, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, ctx->s.nucM, cb.n1, cb.n2, L, cb.Qy, cb.Qx, tyo, txo, zeta, A);
   else k_apply<64><<<ga, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, ctx->s.nucM, cb.n1, cb.n2, L, cb.Qy, cb.Qx, tyo, txo, zeta, A);
+  note_launches(1);
 }
 
 }  // namespace fhs

@@ -265,6 +265,7 @@ static void row_fwd_n(const Cube& cb, const float* x, float2* grid, const float2
   if (!attr) { cudaFuncSetAttribute(k_row_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
   dim3 grd((cb.n1 + S - 1) / S, cb.L);
   k_row_fwd<N><<<grd, NT, sm, st>>>(x, grid, cb.d_scale_r, cb.d_scale_c, tw, Kmax / N, cb.n1, cb.n2, cb.K1);
+  note_launches(1);
 }
 
 template <int N>
@@ -277,6 +278,7 @@ static void row_adj_n(const Cube& cb, const float2* grid, float* out, const floa
   dim3 grd((cb.n1 + S - 1) / S, cb.L);
   k_row_adj<N><<<grd, NT, sm, st>>>(grid, out, cb.d_scale_r, cb.d_scale_c, eta, acc ? 1 : 0, tw, Kmax / N, cb.n1,
                                     cb.n2, cb.K1);
+  note_launches(1);
 }
 
 template <int N>
@@ -289,6 +291,7 @@ static void col_n(const Cube& cb, float2* grid, int ngroups, int gmul, int istri
   dim3 grd(cb.K2 / W, ngroups, cb.L);
   k_col<N><<<grd, NT, sm, st>>>(grid, cb.K1, cb.K2, gmul, istride, twiddle, inv, prune, cb.n1, tw, Kmax / N,
                                 Kmax / cb.K1);
+  note_launches(1);
 }
 
 #define FHS_POW2_SWITCH(n, FN, ...)                  \
@@ -620,6 +623,7 @@ int degrid_parts(const Cube& cb) { return (int)((cb.max_M + 255) / 256); }
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, cudaStream_t st) {
   dim3 grd(degrid_parts(cb), cb.L);
   k_degrid<<<grd, 256, 0, st>>>(grid, cb.d_uv, out, cb.d_vis_off, vis_geom(cb));
+  note_launches(1);
 }
 
 void launch_degrid_pdfb(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
@@ -627,23 +631,27 @@ void launch_degrid_pdfb(const Cube& cb, const float2* grid, const float2* y, con
   dim3 grd(nparts, cb.L);
   k_degrid_pdfb<<<grd, 256, 0, st>>>(grid, cb.d_uv, y, v, d_out, u_prev, cb.d_blk, cb.d_vis_off, vis_geom(cb), cb.B,
                                      partials, nparts);
+  note_launches(1);
 }
 
 void launch_l2ball_partials(const Cube& cb, const float2* z, const float2* y, float2* d, double* partials, int nparts,
                             cudaStream_t st) {
   dim3 grd(nparts, cb.L);
   k_l2ball_partials<<<grd, 256, 0, st>>>(z, y, d, cb.d_blk, cb.d_vis_off, cb.B, partials, nparts);
+  note_launches(1);
 }
 
 void launch_block_finalize(const Cube& cb, const double* partials, int nparts, float* scale, double* out,
                            cudaStream_t st) {
   int n = cb.L * cb.B;
   k_block_finalize<<<(n + 127) / 128, 128, 0, st>>>(partials, nparts, cb.B, cb.L, cb.d_eps, scale, out);
+  note_launches(1);
 }
 
 void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, float2* v, cudaStream_t st) {
   dim3 grd(degrid_parts(cb), cb.L);
   k_l2ball_scale<<<grd, 256, 0, st>>>(d, scale, cb.d_blk, cb.d_vis_off, cb.B, v);
+  note_launches(1);
 }
 
 void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write, float2* grid,
@@ -654,6 +662,7 @@ void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, flo
   size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(float);
   k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
                                vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
+  note_launches(1);
 }
 
 // ---------------------------------------------------- visibility reordering
@@ -671,10 +680,12 @@ __global__ void k_vis_scatter(const int64_t* __restrict__ perm, int64_t n, const
 
 void launch_vis_gather(const int64_t* perm, int64_t n, const float2* in, float2* out, cudaStream_t st) {
   if (n > 0) k_vis_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(perm, n, in, out);
+  note_launches(1);
 }
 
 void launch_vis_scatter(const int64_t* perm, int64_t n, const float2* in, float2* out, cudaStream_t st) {
   if (n > 0) k_vis_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(perm, n, in, out);
+  note_launches(1);
 }
 
 void launch_measure(fhs_ctx* ctx, const Cube& cb, const float* x, float2* y, cudaStream_t st) {

@@ -60,6 +60,7 @@ void launch_primal(const Cube& cb, float* X, float* Xc, const float* A, double* 
                    cudaStream_t st) {
   int64_t n = (int64_t)cb.L * cb.n1 * cb.n2;
   k_primal<<<nparts, 256, 0, st>>>((float4*)X, (float4*)Xc, (const float4*)A, (float)cb.tau, n / 4, partials);
+  note_launches(1);
 }
 
 // Per-channel sums of squares: partials[l][p] over nparts CTAs per channel.
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(256) k_sumsq(const float* __restrict__ a, int6
 void launch_sumsq(const float* a, int64_t n_per_ch, int L, double* partials, int nparts, cudaStream_t st) {
   dim3 g(nparts, L);
   k_sumsq<<<g, 256, 0, st>>>(a, n_per_ch, partials, nparts);
+  note_launches(1);
 }
 
 __global__ void k_scale_ch(float* __restrict__ x, int64_t n, const double* __restrict__ inv) {
@@ -91,6 +93,7 @@ __global__ void k_scale_ch(float* __restrict__ x, int64_t n, const double* __res
 void launch_scale_by_channel(float* x, int64_t n_per_ch, int L, const double* inv, cudaStream_t st) {
   dim3 g(64, L);
   k_scale_ch<<<g, 256, 0, st>>>(x, n_per_ch, inv);
+  note_launches(1);
 }
 
 }  // namespace fhs

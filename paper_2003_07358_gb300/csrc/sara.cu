@@ -211,15 +211,18 @@ void launch_sara_analysis(fhs_ctx* ctx, const Cube& cb, const float* x, float* c
       int mo1 = S.rows[b][j], mo2 = S.cols[b][j];
       int64_t n = (int64_t)L * m1 * mo2;
       k_ana_cols<<<nblk(n, 256), 256, 0, st>>>(in, lx, hx, L, m1, m2, mo2, b);
+      note_launches(1);
       float* llo = (j == kLevels) ? nullptr : ((j & 1) ? llA : llB);
       int64_t n2 = (int64_t)L * mo1 * mo2;
       k_ana_rows<<<nblk(n2, 256), 256, 0, st>>>(lx, hx, llo, coef, S.I, S.off[b][j][0], S.off[b][j][1],
                                                 S.off[b][j][2], S.off[b][kLevels][3], L, m1, mo1, mo2, b);
+      note_launches(1);
       in = llo;
     }
   }
   int64_t N = (int64_t)cb.n1 * cb.n2;
   k_dirac_ana<<<nblk(L * N, 256), 256, 0, st>>>(x, coef, S.I, S.dirac_off, N, L);
+  note_launches(1);
 }
 
 void launch_sara_synthesis(fhs_ctx* ctx, const Cube& cb, const float* coef, float* out, float scale, bool accumulate,
@@ -239,28 +242,34 @@ void launch_sara_synthesis(fhs_ctx* ctx, const Cube& cb, const float* coef, floa
       int64_t n = (int64_t)L * m1 * mo2;
       k_syn_rows<<<nblk(n, 256), 256, 0, st>>>(ll_in, coef, S.I, S.off[b][j][0], S.off[b][j][1], S.off[b][j][2],
                                                S.off[b][kLevels][3], lx, hx, L, m1, mo1, mo2, b);
+      note_launches(1);
       int64_t n2 = (int64_t)L * m1 * m2;
       if (j > 1) {
         float* llo = (ll_in == llA) ? llB : llA;
         k_syn_cols<<<nblk(n2, 256), 256, 0, st>>>(lx, hx, llo, 1.f, 0, L, m1, m2, mo2, b);
+        note_launches(1);
         ll_in = llo;
       } else {
         k_syn_cols<<<nblk(n2, 256), 256, 0, st>>>(lx, hx, out, scale, acc ? 1 : 0, L, m1, m2, mo2, b);
+        note_launches(1);
         acc = true;
       }
     }
   }
   int64_t N = (int64_t)cb.n1 * cb.n2;
   k_dirac_syn<<<nblk(L * N, 256), 256, 0, st>>>(coef, S.I, S.dirac_off, N, L, out, scale, acc ? 1 : 0);
+  note_launches(1);
 }
 
 void launch_l21_dual(const Cube& cb, float* W, const float* coef, const float* theta, cudaStream_t st) {
   float alpha_scale = (float)(cb.mu / cb.kappa);
   k_l21_dual<<<nblk(cb.sara.I, 256), 256, 0, st>>>(W, coef, theta, alpha_scale, cb.sara.I, cb.L);
+  note_launches(1);
 }
 
 void launch_l21_weights(const Cube& cb, const float* coef, float* theta, cudaStream_t st) {
   k_l21_weights<<<nblk(cb.sara.I, 256), 256, 0, st>>>(coef, theta, (float)cb.mu, cb.sara.I, cb.L);
+  note_launches(1);
 }
 
 }  // namespace fhs

@@ -24,7 +24,7 @@ SYMBOLS = [
     "fhs_create", "fhs_destroy", "fhs_get_sizes", "fhs_sync", "fhs_last_error", "fhs_vis_permutation",
     "fhs_vis_to_internal", "fhs_vis_to_user", "fhs_measure", "fhs_adjoint", "fhs_opnorm_sq",
     "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_prox_l21_sara_facets", "fhs_prox_nuclear_facets",
-    "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter",
+    "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
 ]
 
 
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         "fhs_proj_l2ball_blocks": ([vp, i32, vp, vp, vp, dp], i32),
         "fhs_reweight": ([vp, i32, vp, vp, vp], i32),
         "fhs_pdfb_iter": ([vp, C.POINTER(fhs_iterate), i32, C.POINTER(fhs_iter_stats)], i32),
+        "fhs_set_params": ([vp, i32, C.c_double, C.c_double, C.c_double, dp, C.c_double, dp, dp], i32),
+        "fhs_kernel_launches": ([], C.c_uint64),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -248,6 +250,15 @@ class Context:
         if not want_stats:
             return None
         return [{"xi": s.xi, "res_norm": s.res_norm, "eps_norm": s.eps_norm} for s in stats]
+
+    def fhs_set_params(self, cube, tau, zeta, kappa, eta, mu, mu_bar, eps):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (eta, mu_bar, eps)]
+        P = C.POINTER(C.c_double)
+        self._check(self.lib.fhs_set_params(self.h, cube, tau, zeta, kappa, arrs[0].ctypes.data_as(P), mu,
+                                            arrs[1].ctypes.data_as(P), arrs[2].ctypes.data_as(P)))
+
+    def fhs_kernel_launches(self) -> int:
+        return int(self.lib.fhs_kernel_launches())
 
     # ------------------------------------------------------------ helpers
     def new_state(self, cube: int = 0) -> dict:

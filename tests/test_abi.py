@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def header_symbols():
     text = open(os.path.join(ROOT, "include", "fhs.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:fhs_status|const char\*)\s+(fhs_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:fhs_status|const char\*|uint64_t)\s+(fhs_\w+)\s*\(", text, re.M)))
 
 
 @pytest.fixture(scope="module")
