@@ -311,6 +311,7 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     l0 = ctx.fhs_kernel_launches()
+    log(f"timed region starts after {l0} library kernel launches")
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)

@@ -66,6 +66,7 @@ struct Cube {
   NucFacet* d_facets = nullptr;
   float* d_win = nullptr;                    // window tables (y and x windows concatenated)
   int* d_tile_of = nullptr;                  // [n1 + n2]: tile index of each row, then of each column
+  double* d_win64 = nullptr;                 // window tables in FP64 (reweighting Gram)
   float* d_scale_r = nullptr;                // [n1] deapodisation s_r
   float* d_scale_c = nullptr;                // [n2]
   double* d_eps = nullptr;                   // [L*B]

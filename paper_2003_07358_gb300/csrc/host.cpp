@@ -245,7 +245,7 @@ double window_w(int i, int o, int kind) {
 
 // 1-D nuclear facets along one axis: start, end and window per tile.
 void nuclear_axis(int n, int Q, double rho, int kind, std::vector<int>& start, std::vector<int>& end,
-                  std::vector<std::vector<float>>& win) {
+                  std::vector<std::vector<double>>& win) {
   std::vector<int> tb = tile_bounds(n, Q);
   std::vector<int> ov(Q);
   for (int i = 0; i < Q; ++i) ov[i] = i == 0 ? 0 : (int)floor(rho * (tb[i + 1] - tb[i]));
@@ -331,13 +331,14 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
 
   // nuclear facets
   std::vector<int> ys, ye, xs, xe;
-  std::vector<std::vector<float>> wy, wx;
+  std::vector<std::vector<double>> wy, wx;
   nuclear_axis(d.n1, d.Qy, d.overlap, d.window, ys, ye, wy);
   nuclear_axis(d.n2, d.Qx, d.overlap, d.window, xs, xe, wx);
-  std::vector<float> win;
+  std::vector<double> win64;
   std::vector<int> wy_off(d.Qy), wx_off(d.Qx);
-  for (int i = 0; i < d.Qy; ++i) { wy_off[i] = (int)win.size(); win.insert(win.end(), wy[i].begin(), wy[i].end()); }
-  for (int i = 0; i < d.Qx; ++i) { wx_off[i] = (int)win.size(); win.insert(win.end(), wx[i].begin(), wx[i].end()); }
+  for (int i = 0; i < d.Qy; ++i) { wy_off[i] = (int)win64.size(); win64.insert(win64.end(), wy[i].begin(), wy[i].end()); }
+  for (int i = 0; i < d.Qx; ++i) { wx_off[i] = (int)win64.size(); win64.insert(win64.end(), wx[i].begin(), wx[i].end()); }
+  std::vector<float> win(win64.begin(), win64.end());
   cb.facets.clear();
   int64_t poff = 0;
   cb.max_facet_pix = 0;
@@ -435,6 +436,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
   cb.d_tile_off = dalloc<int32_t>(tile_off.size());
   cb.d_facets = dalloc<NucFacet>(cb.facets.size());
   cb.d_win = dalloc<float>(win.size());
+  cb.d_win64 = dalloc<double>(win64.size());
   cb.d_tile_of = dalloc<int>(tile_of.size());
   cb.d_scale_r = dalloc<float>(d.n1);
   cb.d_scale_c = dalloc<float>(d.n2);
@@ -449,6 +451,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
   upload(cb.d_tile_off, tile_off.data(), tile_off.size(), st);
   upload(cb.d_facets, cb.facets.data(), cb.facets.size(), st);
   upload(cb.d_win, win.data(), win.size(), st);
+  upload(cb.d_win64, win64.data(), win64.size(), st);
   upload(cb.d_tile_of, tile_of.data(), tile_of.size(), st);
   upload(cb.d_scale_r, sr.data(), sr.size(), st);
   upload(cb.d_scale_c, sc.data(), sc.size(), st);
@@ -459,7 +462,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
 }
 
 void free_cube(Cube& cb) {
-  void* ps[] = {cb.d_uv, cb.d_blk, cb.d_perm, cb.d_vis_off, cb.d_tile_off, cb.d_facets, cb.d_win, cb.d_tile_of,
+  void* ps[] = {cb.d_uv, cb.d_blk, cb.d_perm, cb.d_vis_off, cb.d_tile_off, cb.d_facets, cb.d_win, cb.d_win64, cb.d_tile_of,
                 cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar};
   for (void* p : ps)
     if (p) cudaFree(p);

@@ -112,6 +112,63 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
   }
 }
 
+// FP64 partial Gram of D_q S~_q x (weights mode of Algorithm 1, once per
+// reweighting cycle): z = wy * wx * x formed and multiplied in FP64 so that
+// the small singular values entering theta_bar = mu_bar / (s + mu_bar) are not
+// limited by rounding z to FP32.
+__global__ void __launch_bounds__(256) k_gram_f64(const float* __restrict__ xc, const NucFacet* __restrict__ facets,
+                                                  const double* __restrict__ win64, int n1, int n2, int L,
+                                                  double* __restrict__ part, int nchunk_max) {
+  __shared__ double z[kGramSub / 2][kMaxL + 1];
+  constexpr int SUB = kGramSub / 2;
+  const int q = blockIdx.y;
+  const NucFacet f = facets[q];
+  const int h = f.r1 - f.r0, w = f.c1 - f.c0;
+  const int Nq = h * w;
+  const int p0 = blockIdx.x * kGramChunk;
+  if (p0 >= Nq) return;
+  const int p1 = min(Nq, p0 + kGramChunk);
+  const int LB = L <= 16 ? 1 : (L <= 32 ? 2 : 4);
+  const int Lp = (L + LB - 1) / LB * LB;
+  const int nb = Lp / LB;
+  const int ta = threadIdx.x / nb, tb = threadIdx.x % nb;
+  const bool active = ta < nb && ta <= tb;
+  double acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const size_t N = (size_t)n1 * n2;
+  for (int s0 = p0; s0 < p1; s0 += SUB) {
+    for (int idx = threadIdx.x; idx < SUB * Lp; idx += blockDim.x) {
+      int pix = idx % SUB, l = idx / SUB;
+      int p = s0 + pix;
+      double val = 0.0;
+      if (p < p1 && l < L) {
+        int rr = p / w, cc = p % w;
+        val = win64[f.wy_off + rr] * win64[f.wx_off + cc] * (double)xc[l * N + (size_t)(f.r0 + rr) * n2 + (f.c0 + cc)];
+      }
+      z[pix][l] = val;
+    }
+    __syncthreads();
+    if (active) {
+      for (int pix = 0; pix < SUB; ++pix)
+        for (int i = 0; i < LB; ++i)
+          for (int j = 0; j < LB; ++j) acc[i][j] = fma(z[pix][ta * LB + i], z[pix][tb * LB + j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  if (active) {
+    double* out = part + ((size_t)q * nchunk_max + blockIdx.x) * L * L;
+    for (int i = 0; i < LB; ++i)
+      for (int j = 0; j < LB; ++j) {
+        int a = ta * LB + i, b = tb * LB + j;
+        if (a < L && b < L) {
+          out[a * L + b] = acc[i][j];
+          out[b * L + a] = acc[i][j];
+        }
+      }
+  }
+}
+
 // One warp per facet: G = sum of partial Grams (FP64, fixed order), cyclic
 // Jacobi eigen-decomposition G = V diag(lambda) V^T, s = sqrt(max(lambda, 0))
 // sorted descending, then either M = V diag(m) V^T with
@@ -286,7 +343,9 @@ void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P,
   const int nch = nchunk_max(cb);
   dim3 gg(nch, Q);
   int use_P = (P != nullptr && !weights_mode) ? 1 : 0;
-  if (L <= 16) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  if (weights_mode)
+    k_gram_f64<<<gg, 256, 0, st>>>(xcheck, cb.d_facets, cb.d_win64, cb.n1, cb.n2, L, ctx->s.gram, nch);
+  else if (L <= 16) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   else if (L <= 32) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   else k_gram<4><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   note_launches(1);
