@@ -25,6 +25,7 @@ SYMBOLS = [
     "fhs_vis_to_internal", "fhs_vis_to_user", "fhs_measure", "fhs_adjoint", "fhs_opnorm_sq",
     "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_prox_l21_sara_facets", "fhs_prox_nuclear_facets",
     "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
+    "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error",
 ]
 
 
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH):
         "fhs_pdfb_iter": ([vp, C.POINTER(fhs_iterate), i32, C.POINTER(fhs_iter_stats)], i32),
         "fhs_set_params": ([vp, i32, C.c_double, C.c_double, C.c_double, dp, C.c_double, dp, dp], i32),
         "fhs_kernel_launches": ([], C.c_uint64),
+        "fhs_proj_l2ball_noalloc": ([vp, vp, i64p, i32, dp, vp, dp, vp], i32),
+        "fhs_noalloc_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -109,6 +112,25 @@ def _ptr(t) -> int | None:
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("libfhs takes contiguous CUDA tensors")
     return t.data_ptr()
+
+
+def fhs_proj_l2ball_noalloc(z, y, seg_off, eps, v_out, want_norms: bool = True, stream=None):
+    """Allocation-free l2-ball projection on plain arrays (no context): segment s
+    of the caller's order gets v = (z - y)(1 - min(1, eps_s / ||z_s - y_s||)).
+    For callers that may not allocate device memory; see include/fhs.h."""
+    import torch
+    lib = load()
+    so = np.ascontiguousarray(seg_off, dtype=np.int64)
+    ep = np.ascontiguousarray(eps, dtype=np.float64)
+    out = np.zeros(so.size - 1, dtype=np.float64) if want_norms else None
+    st = stream if stream is not None else torch.cuda.current_stream()
+    P = C.POINTER(C.c_double)
+    rc = lib.fhs_proj_l2ball_noalloc(_ptr(z), _ptr(y), so.ctypes.data_as(C.POINTER(C.c_int64)), so.size - 1,
+                                     ep.ctypes.data_as(P), _ptr(v_out), out.ctypes.data_as(P) if want_norms else None,
+                                     C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise FhsError(rc, lib.fhs_noalloc_last_error().decode())
+    return out
 
 
 @dataclass
