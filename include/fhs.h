@@ -198,6 +198,12 @@ fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta
  * (Sections 2.3-2.4) on a context before iterating.  Synchronising. */
 fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, double kappa, const double* eta,
                           double mu, const double* mu_bar, const double* eps);
+/* Kernel path used by fhs_pdfb_iter, fhs_prox_l21_sara_facets and fhs_reweight:
+ * FHS_PATH_FAST (default) uses the fused kernels; FHS_PATH_PLAIN the
+ * unfused one-launch-per-pass kernels (the FP32 reference path that the fused
+ * one is measured against).  Both compute the same operators. */
+enum { FHS_PATH_FAST = 0, FHS_PATH_PLAIN = 1 };
+fhs_status fhs_set_path(fhs_ctx* ctx, int32_t path);
 /* Number of CUDA kernels this library has launched in this process so far. */
 uint64_t fhs_kernel_launches(void);
 

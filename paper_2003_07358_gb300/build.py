@@ -43,7 +43,7 @@ def build(verbose: bool = False, force: bool = False, extra: list[str] | None = 
     """Compile csrc/* for sm_103a and link libfhs.so; returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "fhs.h"))
     srcs = sources()
     objs = []

@@ -90,6 +90,8 @@ struct Scratch {
   float* nucM = nullptr;     size_t nucM_elems = 0;     // [Q][L][L]
   float* blk_scale = nullptr;                           // [L*B]
   double* blk_out = nullptr;                            // [2][L*B]
+  float* ll1 = nullptr;                                 // synthesised LL1 band of each basis (fused SARA)
+  int64_t ll1_off[8] = {0};                             // per-basis offsets into ll1
 };
 
 }  // namespace fhs
@@ -102,6 +104,7 @@ struct fhs_ctx {
   int Kmax = 0;
   std::string err;
   bool broken = false;
+  int path = FHS_PATH_FAST;        // FHS_PATH_FAST or FHS_PATH_PLAIN
 };
 
 namespace fhs {
@@ -140,6 +143,10 @@ void launch_sara_synthesis(fhs_ctx* ctx, const Cube& cb, const float* coef, floa
                            bool accumulate, cudaStream_t st);
 void launch_l21_dual(const Cube& cb, float* W, const float* coef, const float* theta, cudaStream_t st);
 void launch_l21_weights(const Cube& cb, const float* coef, float* theta, cudaStream_t st);
+// fused analysis + l2,1 dual (+ synthesis into A), or weights mode (theta_out)
+void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, const float* theta, float* A,
+                      float* theta_out, bool weights, cudaStream_t st);
+bool sara_fast_supported(const Cube& cb);
 
 // nuclear (nuclear.cu)
 void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P, const float* theta_bar,

@@ -489,8 +489,15 @@ void alloc_scratch(fhs_ctx* ctx) {
     nm = std::max(nm, (size_t)cb.facets.size() * L * L);
     lb = std::max(lb, L * cb.B);
   }
+  size_t ll1 = 0;
+  for (const Cube& cb : ctx->cubes) {
+    size_t tot = 0;
+    for (int b = 0; b < 8; ++b) tot += (size_t)cb.L * cb.sara.rows[b][1] * cb.sara.cols[b][1];
+    ll1 = std::max(ll1, tot);
+  }
   s.grid = dalloc<float2>(grid); s.grid_elems = grid;
-  s.coef = dalloc<float>(coef); s.coef_elems = coef;
+  s.coef_elems = coef;          // allocated on first use of the plain path (ensure_coef)
+  s.ll1 = dalloc<float>(ll1);
   s.t0 = dalloc<float>(tlx); s.t1 = dalloc<float>(tlx);
   s.t2 = dalloc<float>(tll); s.t3 = dalloc<float>(tll);
   s.t_elems = tlx;
@@ -506,7 +513,7 @@ void alloc_scratch(fhs_ctx* ctx) {
 
 void free_scratch(Scratch& s) {
   void* ps[] = {s.grid, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.img2, s.vis, s.red, s.gram, s.nucM, s.blk_scale,
-                s.blk_out};
+                s.blk_out, s.ll1};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (s.red_host) cudaFreeHost(s.red_host);
@@ -518,11 +525,33 @@ const Cube& get_cube(fhs_ctx* ctx, int32_t c) {
 }
 
 // ------------------------------------------------------ composite steps
+// Per-basis offsets of the synthesised LL1 bands used by the fused SARA path.
+void set_ll1_offsets(fhs_ctx* ctx, const Cube& cb) {
+  int64_t off = 0;
+  for (int b = 0; b < 8; ++b) {
+    ctx->s.ll1_off[b] = off;
+    off += (int64_t)cb.L * cb.sara.rows[b][1] * cb.sara.cols[b][1];
+  }
+}
+
+// The plain path's [L][I] coefficient buffer, allocated on first use.
+void ensure_coef(fhs_ctx* ctx) {
+  if (!ctx->s.coef) ctx->s.coef = dalloc<float>(ctx->s.coef_elems);
+}
+
+bool use_fast(fhs_ctx* ctx, const Cube& cb) { return ctx->path == FHS_PATH_FAST && sara_fast_supported(cb); }
+
 void sara_dual(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* W, const float* theta, float* A) {
   cudaStream_t st = ctx->stream;
-  launch_sara_analysis(ctx, cb, xcheck, ctx->s.coef, st);
-  launch_l21_dual(cb, W, ctx->s.coef, theta, st);
-  launch_sara_synthesis(ctx, cb, W, A, (float)cb.kappa, true, st);
+  if (use_fast(ctx, cb)) {
+    set_ll1_offsets(ctx, cb);
+    launch_sara_fast(ctx, cb, xcheck, W, theta, A, nullptr, false, st);
+  } else {
+    ensure_coef(ctx);
+    launch_sara_analysis(ctx, cb, xcheck, ctx->s.coef, st);
+    launch_l21_dual(cb, W, ctx->s.coef, theta, st);
+    launch_sara_synthesis(ctx, cb, W, A, (float)cb.kappa, true, st);
+  }
   check_launch("sara dual");
 }
 
@@ -775,8 +804,13 @@ fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta
     FHS_REQUIRE(x && theta && theta_bar, FHS_ERR_INVALID_ARG, "NULL array");
     const Cube& cb = get_cube(ctx, cube);
     cudaStream_t st = ctx->stream;
-    launch_sara_analysis(ctx, cb, x, ctx->s.coef, st);
-    launch_l21_weights(cb, ctx->s.coef, theta, st);
+    if (use_fast(ctx, cb)) {
+      launch_sara_fast(ctx, cb, x, nullptr, nullptr, nullptr, theta, true, st);
+    } else {
+      ensure_coef(ctx);
+      launch_sara_analysis(ctx, cb, x, ctx->s.coef, st);
+      launch_l21_weights(cb, ctx->s.coef, theta, st);
+    }
     launch_nuclear(ctx, cb, x, nullptr, nullptr, nullptr, true, theta_bar, st);
     check_launch("reweight");
   });
@@ -809,6 +843,13 @@ fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, d
 }
 
 uint64_t fhs_kernel_launches(void) { return g_launches.load(); }
+
+fhs_status fhs_set_path(fhs_ctx* ctx, int32_t path) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(path == FHS_PATH_FAST || path == FHS_PATH_PLAIN, FHS_ERR_INVALID_ARG, "unknown path");
+    ctx->path = path;
+  });
+}
 
 fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fhs_iter_stats* stats) {
   return guarded(ctx, [&] {

@@ -505,23 +505,39 @@ __global__ void __launch_bounds__(256) k_l2ball_partials(const float2* __restric
 
 // Per (channel, block): sum the CTA partials in order; scale = max(0, 1 - eps/||d||);
 // out[2][L*B] = (||d||, ||y - u||) in FP64.
-__global__ void k_block_finalize(const double* __restrict__ partials, int nparts, int B, int L,
-                                 const double* __restrict__ eps, float* __restrict__ scale, double* __restrict__ out) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= L * B) return;
-  int l = k / B, b = k % B;
+// One CTA per (channel, block): the CTA partials are summed in a fixed order
+// (thread t takes p = t, t + 256, ..., then a fixed shared-memory tree), so the
+// result does not depend on scheduling.  scale = max(0, 1 - eps/||d||);
+// out[2][L*B] = (||d||, ||y - u||) in FP64.
+__global__ void __launch_bounds__(256) k_block_finalize(const double* __restrict__ partials, int nparts, int B, int L,
+                                                        const double* __restrict__ eps, float* __restrict__ scale,
+                                                        double* __restrict__ out) {
+  __shared__ double s0s[256], s1s[256];
+  const int k = blockIdx.x;
+  const int l = k / B, b = k % B;
   double s0 = 0.0, s1 = 0.0;
-  for (int p = 0; p < nparts; ++p) {
+  for (int p = threadIdx.x; p < nparts; p += 256) {
     const double* pp = partials + ((size_t)l * nparts + p) * 2 * B;
     s0 += pp[b];
     s1 += pp[B + b];
   }
-  double dn = sqrt(s0);
+  s0s[threadIdx.x] = s0;
+  s1s[threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s0s[threadIdx.x] += s0s[threadIdx.x + w];
+      s1s[threadIdx.x] += s1s[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double dn = sqrt(s0s[0]);
   double e = eps ? eps[k] : 0.0;
   if (scale) scale[k] = (float)(dn > e ? 1.0 - e / dn : 0.0);
   if (out) {
     out[k] = dn;
-    out[L * B + k] = sqrt(s1);
+    out[L * B + k] = sqrt(s1s[0]);
   }
 }
 
@@ -644,7 +660,7 @@ void launch_l2ball_partials(const Cube& cb, const float2* z, const float2* y, fl
 void launch_block_finalize(const Cube& cb, const double* partials, int nparts, float* scale, double* out,
                            cudaStream_t st) {
   int n = cb.L * cb.B;
-  k_block_finalize<<<(n + 127) / 128, 128, 0, st>>>(partials, nparts, cb.B, cb.L, cb.d_eps, scale, out);
+  k_block_finalize<<<n, 256, 0, st>>>(partials, nparts, cb.B, cb.L, cb.d_eps, scale, out);
   note_launches(1);
 }
 

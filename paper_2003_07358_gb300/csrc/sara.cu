@@ -273,3 +273,5 @@ void launch_l21_weights(const Cube& cb, const float* coef, float* theta, cudaStr
 }
 
 }  // namespace fhs
+
+#include "sara_fast.cuh"
