@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ops", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -329,6 +330,24 @@ def main():
     value = world * 1000.0 / ms
     log(f"{ms:.1f} ms per iteration")
 
+    # the plain FP32 path (one launch per pass, unfused) on the same state, for the speed-up
+    plain = None
+    if args.plain_steps > 0:
+        ctx.fhs_set_path("plain")
+        ctx.fhs_pdfb_iter(its, 1, want_stats=False)
+        barrier()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.plain_steps):
+            ctx.fhs_pdfb_iter(its, 1, want_stats=False)
+        p1.record(stream)
+        barrier()
+        ctx.fhs_set_path("fast")
+        pms = p0.elapsed_time(p1) / args.plain_steps
+        plain = {"ms_per_step": pms, "value": world * 1000.0 / pms, "speedup_fast_over_plain": pms / ms}
+        log(f"plain path {pms:.1f} ms per iteration")
+
     # per-operator times through their own C-ABI calls (same stream, CUDA events)
     hbm, peak_kind = peaks()
     ops = {}
@@ -411,10 +430,10 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": spec.name, "n": spec.n, "L": spec.L, "subcubes": spec.C,
                            "facets": f"{spec.Q}x{spec.Q}", "vis_per_channel": spec.M, "blocks": spec.B,
-                           "path": "FP32 (plain kernels, FP64 reductions)",
+                           "path": "FP32 fused kernels (FP64 reductions)",
                            "l2": "working set ~100 GB >> 129 MB L2; no flush"},
                 "roofline": roofline, "operators": ops, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clocks, "gpu_launches": launches}
+                "plain_fp32_path": plain, "clocks": clocks, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

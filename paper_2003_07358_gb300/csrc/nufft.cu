@@ -78,7 +78,15 @@ __device__ __forceinline__ void dftR(float2* v, bool inv) {
 
 // One Stockham autosort pass over S interleaved sequences of length N held in
 // shared memory as buf[n * S + s].  NT threads, each owning (N/R)*S/NT butterflies.
-template <int N, int S, int NT, int R>
+// PAD: one float2 of padding after every 8 elements (single-sequence buffers),
+// which makes the stride-R stores of the first passes bank-conflict-free.
+template <bool PAD>
+__device__ __forceinline__ int pix(int e) { return PAD ? e + (e >> 3) : e; }
+
+// SEQ: sequence-major layout buf[s * N + n] with butterflies enumerated j-fastest
+// (used for row transforms); otherwise interleaved buf[n * S + s], s-fastest
+// (column transforms: S = W adjacent grid columns).
+template <int N, int S, int NT, int R, bool PAD = false, bool SEQ = false>
 __device__ __forceinline__ void stockham_pass(float2* buf, int Ns, const float2* __restrict__ tw,
                                               int twstride, bool inv) {
   constexpr int NB = (N / R) * S;
@@ -88,10 +96,14 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int Ns, const float2*
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     int item = threadIdx.x + p * NT;
-    int s = item % S, j = item / S;
+    int s = SEQ ? item / (N / R) : item % S;
+    int j = SEQ ? item % (N / R) : item / S;
     int k = j % Ns;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[p][r] = buf[(j + r * (N / R)) * S + s];
+    for (int r = 0; r < R; ++r) {
+      int n = j + r * (N / R);
+      v[p][r] = buf[pix<PAD>(SEQ ? s * N + n : n * S + s)];
+    }
     if (Ns > 1) {
       int step = (N / (Ns * R)) * twstride;
 #pragma unroll
@@ -106,11 +118,15 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int Ns, const float2*
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     int item = threadIdx.x + p * NT;
-    int s = item % S, j = item / S;
+    int s = SEQ ? item / (N / R) : item % S;
+    int j = SEQ ? item % (N / R) : item / S;
     int k = j % Ns;
     int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[(base + r * Ns) * S + s] = v[p][r];
+    for (int r = 0; r < R; ++r) {
+      int n = base + r * Ns;
+      buf[pix<PAD>(SEQ ? s * N + n : n * S + s)] = v[p][r];
+    }
   }
   __syncthreads();
 }
@@ -119,17 +135,17 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 
 // In-place DFT of S interleaved length-N sequences in shared memory.
 // twstride = Kmax / N (table holds exp(-2 pi i k / Kmax)).
-template <int N, int S, int NT>
+template <int N, int S, int NT, bool PAD = false, bool SEQ = false>
 __device__ __forceinline__ void smem_fft(float2* buf, const float2* __restrict__ tw, int twstride, bool inv) {
   constexpr int LOG = ilog2c(N);
   int Ns = 1;
 #pragma unroll 1
   for (int p = 0; p < LOG / 3; ++p) {
-    stockham_pass<N, S, NT, 8>(buf, Ns, tw, twstride, inv);
+    stockham_pass<N, S, NT, 8, PAD, SEQ>(buf, Ns, tw, twstride, inv);
     Ns *= 8;
   }
-  if constexpr (LOG % 3 == 2) stockham_pass<N, S, NT, 4>(buf, Ns, tw, twstride, inv);
-  if constexpr (LOG % 3 == 1) stockham_pass<N, S, NT, 2>(buf, Ns, tw, twstride, inv);
+  if constexpr (LOG % 3 == 2) stockham_pass<N, S, NT, 4, PAD, SEQ>(buf, Ns, tw, twstride, inv);
+  if constexpr (LOG % 3 == 1) stockham_pass<N, S, NT, 2, PAD, SEQ>(buf, Ns, tw, twstride, inv);
 }
 
 // sequences per CTA for row transforms and columns per CTA for column transforms
@@ -137,7 +153,6 @@ template <int N> struct RowCfg { static constexpr int S = N >= 2048 ? 1 : 2048 /
 template <int N> struct ColCfg { static constexpr int W = N <= 512 ? 32 : 16; static constexpr int NT = N * W / 16; };
 
 // Physical row of frequency row k when the column DFT used two passes.
-__device__ __forceinline__ int phys_row(int k, int N1c, int N2c) { return (k % N1c) * N2c + k / N1c; }
 
 // ------------------------------------------------------------ row kernels
 // Z then row DFT: pixel rows r0..r0+S-1 of channel blockIdx.y -> grid rows (r - n1/2) mod K1.
@@ -321,6 +336,10 @@ static void col_n(const Cube& cb, float2* grid, int ngroups, int gmul, int istri
   }
 
 void launch_fft_forward(fhs_ctx* ctx, const Cube& cb, const float* x, float2* grid, cudaStream_t st) {
+  if (ctx->path == FHS_PATH_FAST) {
+    launch_fft_forward_fast(ctx, cb, x, grid, st);
+    return;
+  }
   FHS_POW2_SWITCH(cb.K2, row_fwd_n, cb, x, grid, ctx->d_tw, ctx->Kmax, st);
   // step A: groups g < N2c, rows N2c*i + g; twiddle after unless single pass
   FHS_COL_SWITCH(cb.N1c, col_n, cb, grid, cb.N2c, 1, cb.N2c, cb.N2c > 1 ? 1 : 0, 0, 1, ctx->d_tw, ctx->Kmax, st);
@@ -332,12 +351,18 @@ void launch_fft_forward(fhs_ctx* ctx, const Cube& cb, const float* x, float2* gr
 
 void launch_fft_adjoint(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta, bool accumulate,
                         cudaStream_t st) {
+  if (ctx->path == FHS_PATH_FAST) {
+    launch_fft_adjoint_fast(ctx, cb, grid, out, eta, accumulate, st);
+    return;
+  }
   if (cb.N2c > 1) {
     FHS_COL_SWITCH(cb.N2c, col_n, cb, grid, cb.N1c, cb.N2c, 1, 0, 1, 0, ctx->d_tw, ctx->Kmax, st);
   }
   FHS_COL_SWITCH(cb.N1c, col_n, cb, grid, cb.N2c, 1, cb.N2c, cb.N2c > 1 ? 1 : 0, 1, 1, ctx->d_tw, ctx->Kmax, st);
   FHS_POW2_SWITCH(cb.K2, row_adj_n, cb, grid, out, eta, accumulate, ctx->d_tw, ctx->Kmax, st);
 }
+
+#include "fft_fast.cuh"
 
 // ------------------------------------------------------ Kaiser-Bessel taps
 struct TapConst {
@@ -375,8 +400,14 @@ __device__ __forceinline__ int kb_weights(float om, float hi, float lo, float* w
 // --------------------------------------------------------- degridding G
 struct VisGeom {
   int K1, K2, N1c, N2c;
+  int lg1, lg2;          // log2(N1c), log2(N2c)
   TapConst tc;
 };
+
+// Physical row of frequency row k (N1c, N2c powers of two): shifts, no division.
+__device__ __forceinline__ int phys_row2(int k, const VisGeom& vg) {
+  return ((k & (vg.N1c - 1)) << vg.lg2) | (k >> vg.lg1);
+}
 
 __device__ __forceinline__ float2 degrid_one(const float2* __restrict__ g, float2 uv, const VisGeom& vg) {
   float wr[kTaps], wc[kTaps];
@@ -385,7 +416,7 @@ __device__ __forceinline__ float2 degrid_one(const float2* __restrict__ g, float
   float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
   for (int a = 0; a < kTaps; ++a) {
-    int row = phys_row((kr + a) & (vg.K1 - 1), vg.N1c, vg.N2c);
+    int row = phys_row2((kr + a) & (vg.K1 - 1), vg);
     const float2* gr = g + (size_t)row * vg.K2;
     float2 racc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -565,12 +596,13 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
                                               const int64_t* __restrict__ vis_off, float2* __restrict__ grid,
                                               VisGeom vg, int T, int ntr, int ntc, int B) {
   extern __shared__ float sacc[];
+  const int TP = T + 1;                  // padded row stride: banks (row + col) mod 32
   float* are = sacc;
-  float* aim = sacc + T * T;
+  float* aim = sacc + T * TP;
   const int l = blockIdx.y;
   const int tau = blockIdx.x;
   const int tr = tau / ntc, tc = tau % ntc;
-  for (int k = threadIdx.x; k < 2 * T * T; k += blockDim.x) sacc[k] = 0.f;
+  for (int k = threadIdx.x; k < 2 * T * TP; k += blockDim.x) sacc[k] = 0.f;
   __syncthreads();
   const int64_t vbase = vis_off[l];
   const int32_t* toff = tile_off + (size_t)l * (ntr * ntc * 4 + 1);
@@ -596,23 +628,22 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
       float wr[kTaps], wc[kTaps];
       int kr = kb_weights(w.y, vg.tc.hi_r, vg.tc.lo_r, wr);
       int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
-      int lr = (kr & (vg.K1 - 1)) - sr * T;   // start of the footprint in the source tile
-      int lc = (kc & (vg.K2 - 1)) - sc * T;
+      // footprint start in the source tile, then the taps of quadrant (dr, dc)
+      // relative to this tile: rows lr + a - dr T, a in [a0, a1)
+      const int lr = (kr & (vg.K1 - 1)) - sr * T - dr * T;
+      const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
+      const int a0 = max(0, -lr), a1 = min(kTaps, T - lr);
+      const int b0 = max(0, -lc), b1 = min(kTaps, T - lc);
 #pragma unroll
       for (int a = 0; a < kTaps; ++a) {
-        int rr = lr + a;
-        if ((rr >= T) != (dr == 1)) continue;
-        rr -= dr * T;
-        if (rr < 0 || rr >= T) continue;
-        float va = wr[a] * val.x, vb = wr[a] * val.y;
+        if (a < a0 || a >= a1) continue;
+        const int rowoff = (lr + a) * TP + lc;
+        const float va = wr[a] * val.x, vb = wr[a] * val.y;
 #pragma unroll
         for (int b = 0; b < kTaps; ++b) {
-          int cc = lc + b;
-          if ((cc >= T) != (dc == 1)) continue;
-          cc -= dc * T;
-          if (cc < 0 || cc >= T) continue;
-          atomicAdd(&are[rr * T + cc], wc[b] * va);
-          atomicAdd(&aim[rr * T + cc], wc[b] * vb);
+          if (b < b0 || b >= b1) continue;
+          atomicAdd(&are[rowoff + b], wc[b] * va);
+          atomicAdd(&aim[rowoff + b], wc[b] * vb);
         }
       }
     }
@@ -621,8 +652,8 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
   float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
   for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
     int rr = k / T, cc = k % T;
-    int row = phys_row(tr * T + rr, vg.N1c, vg.N2c);
-    gl[(size_t)row * vg.K2 + tc * T + cc] = make_float2(are[k], aim[k]);
+    int row = phys_row2(tr * T + rr, vg);
+    gl[(size_t)row * vg.K2 + tc * T + cc] = make_float2(are[rr * TP + cc], aim[rr * TP + cc]);
   }
 }
 
@@ -630,6 +661,8 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
 static VisGeom vis_geom(const Cube& cb) {
   VisGeom vg;
   vg.K1 = cb.K1; vg.K2 = cb.K2; vg.N1c = cb.N1c; vg.N2c = cb.N2c;
+  vg.lg1 = __builtin_ctz(cb.N1c);
+  vg.lg2 = __builtin_ctz(cb.N2c);
   vg.tc = tap_const(cb.K1, cb.K2);
   return vg;
 }
@@ -675,7 +708,7 @@ void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, flo
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
-  size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(float);
+  size_t sm = 2 * (size_t)cb.tile * (cb.tile + 1) * sizeof(float);
   k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
                                vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);

@@ -53,13 +53,21 @@ struct AnaArgs {
   int weights;
 };
 
-__device__ __forceinline__ void fa_stage(const AnaArgs& a, float* tin, int l, int r_in0, int c_in0, int IN) {
+// Stage channel l: its input tile (with halo, zero outside the signal) and,
+// in dual mode, this thread's W values of the channel into zb[s][l][tid].
+__device__ __forceinline__ void fa_stage(const AnaArgs& a, float* tin, float* zb, int l, int r_in0, int c_in0, int IN,
+                                         bool valid, int64_t pos) {
   const float* inl = a.in + (size_t)l * a.m1 * a.m2;
   for (int idx = threadIdx.x; idx < IN * IN; idx += blockDim.x) {
     int r = idx / IN, c = idx % IN;
     int gr = r_in0 + r, gc = c_in0 + c;
     bool v = gr >= 0 && gr < a.m1 && gc >= 0 && gc < a.m2;
     cp_async4(&tin[r * (kInMax + 1) + c], v ? inl + (size_t)gr * a.m2 + gc : inl, v);
+  }
+  const float* Wl = a.W ? a.W + (size_t)l * a.I : inl;
+  for (int s = 0; s < a.nsub; ++s) {
+    bool v = valid && !a.weights;
+    cp_async4(&zb[(s * a.L + l) * (kTK * kTK) + threadIdx.x], v ? Wl + a.off[s] + pos : inl, v);
   }
   cp_async_commit();
 }
@@ -80,11 +88,11 @@ __global__ void __launch_bounds__(256) k_fa_prox(AnaArgs a) {
   const bool valid = (k0 + tk < a.mo1) && (c0 + tc < a.mo2);
   const int64_t pos = (int64_t)(k0 + tk) * a.mo2 + (c0 + tc);
   const float third = 1.f / 3.f;
-  fa_stage(a, tin0, 0, r_in0, c_in0, IN);
+  fa_stage(a, tin0, zb, 0, r_in0, c_in0, IN, valid, pos);
   for (int l = 0; l < a.L; ++l) {
     float* tin = (l & 1) ? tin1 : tin0;
     if (l + 1 < a.L) {
-      fa_stage(a, (l & 1) ? tin0 : tin1, l + 1, r_in0, c_in0, IN);
+      fa_stage(a, (l & 1) ? tin0 : tin1, zb, l + 1, r_in0, c_in0, IN, valid, pos);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -117,14 +125,9 @@ __global__ void __launch_bounds__(256) k_fa_prox(AnaArgs a) {
       }
       if (a.ll_out) a.ll_out[(size_t)l * a.mo1 * a.mo2 + pos] = ll;
       float cf[4] = {d0 * third, d1 * third, d2 * third, ll * third};
-      const float* Wl = a.W + (size_t)l * a.I;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (s < a.nsub) {
-          float w = a.weights ? 0.f : Wl[a.off[s] + pos];
-          zb[(s * a.L + l) * (kTK * kTK) + threadIdx.x] = w + cf[s];
-        }
-      }
+      for (int s = 0; s < 4; ++s)
+        if (s < a.nsub) zb[(s * a.L + l) * (kTK * kTK) + threadIdx.x] += cf[s];   // W staged (0 in weights mode)
     }
     __syncthreads();
   }

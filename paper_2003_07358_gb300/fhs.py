@@ -25,8 +25,9 @@ SYMBOLS = [
     "fhs_vis_to_internal", "fhs_vis_to_user", "fhs_measure", "fhs_adjoint", "fhs_opnorm_sq",
     "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_prox_l21_sara_facets", "fhs_prox_nuclear_facets",
     "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
-    "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error",
+    "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path",
 ]
+FHS_PATH = {"fast": 0, "plain": 1}
 
 
 class FhsError(RuntimeError):
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
         "fhs_kernel_launches": ([], C.c_uint64),
         "fhs_proj_l2ball_noalloc": ([vp, vp, i64p, i32, dp, vp, dp, vp], i32),
         "fhs_noalloc_last_error": ([], C.c_char_p),
+        "fhs_set_path": ([vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -278,6 +280,10 @@ class Context:
         P = C.POINTER(C.c_double)
         self._check(self.lib.fhs_set_params(self.h, cube, tau, zeta, kappa, arrs[0].ctypes.data_as(P), mu,
                                             arrs[1].ctypes.data_as(P), arrs[2].ctypes.data_as(P)))
+
+    def fhs_set_path(self, path: str):
+        """'fast' (fused kernels, default) or 'plain' (one launch per pass)."""
+        self._check(self.lib.fhs_set_path(self.h, FHS_PATH[path]))
 
     def fhs_kernel_launches(self) -> int:
         return int(self.lib.fhs_kernel_launches())

@@ -38,12 +38,20 @@ def case(request):
     ctx.close()
 
 
+@pytest.fixture(params=["fast", "plain"])
+def path(request, case):
+    ctx = case[4]
+    ctx.fhs_set_path(request.param)
+    yield request.param
+    ctx.fhs_set_path("fast")
+
+
 def elementwise_ok(got, ref, tol=REL_TOL):
     got, ref = np.asarray(got), np.asarray(ref)
     return np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref)) + 1e-30
 
 
-def test_measure(case):
+def test_measure(case, path):
     _, spec, inp, prob, ctx = case
     x = inp.x_true
     y = torch.empty(prob.uv.shape[0], dtype=torch.complex64, device="cuda")
@@ -54,7 +62,7 @@ def test_measure(case):
     assert elementwise_ok(got, ref, 4 * REL_TOL)
 
 
-def test_adjoint(case):
+def test_adjoint(case, path):
     _, spec, inp, prob, ctx = case
     rng = np.random.default_rng(1)
     v = rng.standard_normal(prob.uv.shape[0]) + 1j * rng.standard_normal(prob.uv.shape[0])
@@ -67,7 +75,7 @@ def test_adjoint(case):
     assert elementwise_ok(got, ref, 4 * REL_TOL)
 
 
-def test_adjoint_identity_on_gpu(case):
+def test_adjoint_identity_on_gpu(case, path):
     _, spec, inp, prob, ctx = case
     rng = np.random.default_rng(2)
     x = rng.standard_normal((prob.L, prob.n1, prob.n2))
@@ -100,7 +108,7 @@ def test_sara_analysis_and_synthesis(case):
     assert rel_err(xs.cpu().numpy(), ref) < REL_TOL
 
 
-def test_prox_l21_sara_facets(case):
+def test_prox_l21_sara_facets(case, path):
     _, spec, inp, prob, ctx = case
     rng = np.random.default_rng(4)
     I = ctx.sizes(0)["n_coef"]
@@ -156,7 +164,7 @@ def test_proj_l2ball_blocks(case):
     assert rel_err(got, ref) < REL_TOL
 
 
-def test_reweight(case):
+def test_reweight(case, path):
     _, spec, inp, prob, ctx = case
     x = inp.x_true.astype(np.float32).astype(np.float64)
     I = ctx.sizes(0)["n_coef"]
@@ -228,9 +236,11 @@ def test_pdfb_end_to_end_tiny_with_reweight():
     ctx.close()
 
 
-def test_pdfb_end_to_end_faceted_few_iterations():
+@pytest.mark.parametrize("kpath", ["fast", "plain"])
+def test_pdfb_end_to_end_faceted_few_iterations(kpath):
     spec, inp, prob = make_problem("faceted", L=6)
     ctx = make_context(prob, torch)
+    ctx.fhs_set_path(kpath)
     Xg, stats, stg = _gpu_iterate(ctx, prob, 5)
     st, out = _oracle_iterate(prob, 5)
     assert rel_err(Xg, st.X) < 1e-4
