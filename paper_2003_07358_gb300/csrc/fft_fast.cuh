@@ -10,8 +10,7 @@
 // then step A^H with the crop, Z^T, real part and eta fused into its store.
 // Row transforms use a sequence-major shared buffer padded every 8 elements,
 // which makes the Stockham stores bank-conflict-free.
-
-namespace fhs {
+// Included inside namespace fhs of nufft.cu (it uses that file's FFT building blocks).
 
 __device__ __forceinline__ int colmap(int cc, int n2, int K2) { return cc < n2 / 2 ? cc : K2 - n2 + cc; }
 
@@ -208,5 +207,3 @@ void launch_fft_adjoint_fast(fhs_ctx* ctx, const Cube& cb, float2* grid, float* 
   if (cb.N2c > 1) { FHS_COL_SWITCH(cb.N2c, colB_n, cb, grid, 1, ctx->d_tw, ctx->Kmax, st); }
   FHS_COL_SWITCH(cb.N1c, colA_adj_n, cb, grid, out, eta, accumulate, ctx->d_tw, ctx->Kmax, st);
 }
-
-}  // namespace fhs
