@@ -105,11 +105,30 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int Ns, const float2*
       v[p][r] = buf[pix<PAD>(SEQ ? s * N + n : n * S + s)];
     }
     if (Ns > 1) {
+      // twiddles w^r, w = exp(-2 pi i k / (Ns R)): two table loads (w, w^4 or w^2),
+      // the other powers by at most two complex products
       int step = (N / (Ns * R)) * twstride;
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(&tw[r * k * step]);
-        v[p][r] = cmul(v[p][r], inv ? cconj(w) : w);
+      float2 w1 = __ldg(&tw[k * step]);
+      if (inv) w1 = cconj(w1);
+      if constexpr (R == 2) {
+        v[p][1] = cmul(v[p][1], w1);
+      } else if constexpr (R == 4) {
+        float2 w2 = __ldg(&tw[2 * k * step]);
+        if (inv) w2 = cconj(w2);
+        v[p][1] = cmul(v[p][1], w1);
+        v[p][2] = cmul(v[p][2], w2);
+        v[p][3] = cmul(v[p][3], cmul(w1, w2));
+      } else {
+        float2 w4 = __ldg(&tw[4 * k * step]);
+        if (inv) w4 = cconj(w4);
+        float2 w2 = cmul(w1, w1), w3 = cmul(w1, w2);
+        v[p][1] = cmul(v[p][1], w1);
+        v[p][2] = cmul(v[p][2], w2);
+        v[p][3] = cmul(v[p][3], w3);
+        v[p][4] = cmul(v[p][4], w4);
+        v[p][5] = cmul(v[p][5], cmul(w4, w1));
+        v[p][6] = cmul(v[p][6], cmul(w4, w2));
+        v[p][7] = cmul(v[p][7], cmul(w4, w3));
       }
     }
     dftR<R>(v[p], inv);

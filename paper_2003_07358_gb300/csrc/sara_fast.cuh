@@ -216,44 +216,45 @@ __device__ __forceinline__ void fs_tile(const SynLevel& s, int b, int l, int r0,
     tc[band * TS + kr * (kKnMax + 1) + kc] = v;
   }
   __syncthreads();
-  // y synthesis: lx[i][kc] = sum_k h[2k+1-i] LL[k][kc] + g[2k+1-i] d1[k][kc]; hx with d0, d2
+  // y synthesis, polyphase: output row i = r0 + il (r0 even), m = il / 2, p = il % 2;
+  // a[2m + p] = sum_{q < F/2} f[2q + 1 - p] c[m + q] (no bounds tests: the tile is zero-padded)
   for (int idx = threadIdx.x; idx < kTO * KN; idx += blockDim.x) {
     int il = idx / KN, kc = idx % KN;
-    int i = r0 + il;
+    int p = il & 1, m = il >> 1;
     float sl = 0.f, sx = 0.f;
-    int klo_i = i / 2, khi_i = (i + F - 2) / 2;
-    for (int k = klo_i; k <= khi_i; ++k) {
-      int t = 2 * k + 1 - i;
-      if (t < 0 || t >= F) continue;
-      int kr = k - klo;
+    for (int q = 0; q < F / 2; ++q) {
+      int t = 2 * q + 1 - p;
       float h = c_filt.h[b][t], g = c_filt.g[b][t];
-      sl = fmaf(h, tc[0 * TS + kr * (kKnMax + 1) + kc], sl);
-      sl = fmaf(g, tc[2 * TS + kr * (kKnMax + 1) + kc], sl);
-      sx = fmaf(h, tc[1 * TS + kr * (kKnMax + 1) + kc], sx);
-      sx = fmaf(g, tc[3 * TS + kr * (kKnMax + 1) + kc], sx);
+      int o = (m + q) * (kKnMax + 1) + kc;
+      sl = fmaf(h, tc[o], fmaf(g, tc[2 * TS + o], sl));
+      sx = fmaf(h, tc[TS + o], fmaf(g, tc[3 * TS + o], sx));
     }
     lx[il * (kKnMax + 1) + kc] = sl;
     hx[il * (kKnMax + 1) + kc] = sx;
   }
   __syncthreads();
-  // x synthesis
-  const int tx = threadIdx.x % kTO, ty = threadIdx.x / kTO;
-  const int j = c0 + tx;
-  const int kclo = j / 2, kchi = (j + F - 2) / 2;
+  // x synthesis, polyphase, parity uniform per warp (see fs_pos)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = w & 1, m = lane & 15;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int il = ty + 8 * q;
+  for (int qq = 0; qq < 4; ++qq) {
+    int il = (w >> 1) * 2 + (lane >> 4) + 8 * qq;
     float v = 0.f;
-    for (int k = kclo; k <= kchi; ++k) {
-      int t = 2 * k + 1 - j;
-      if (t < 0 || t >= F) continue;
-      int kc = k - clo;
-      v = fmaf(c_filt.h[b][t], lx[il * (kKnMax + 1) + kc], v);
-      v = fmaf(c_filt.g[b][t], hx[il * (kKnMax + 1) + kc], v);
+    for (int q = 0; q < F / 2; ++q) {
+      int t = 2 * q + 1 - p;
+      int o = il * (kKnMax + 1) + m + q;
+      v = fmaf(c_filt.h[b][t], lx[o], fmaf(c_filt.g[b][t], hx[o], v));
     }
-    acc[q] += v;
+    acc[qq] += v;
   }
   __syncthreads();
+}
+
+// Output position of accumulator qq of this thread in the 32x32 tile.
+__device__ __forceinline__ void fs_pos(int qq, int& il, int& jc) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  il = (w >> 1) * 2 + (lane >> 4) + 8 * qq;
+  jc = 2 * (lane & 15) + (w & 1);
 }
 
 __global__ void __launch_bounds__(256) k_fs_level(SynLevel s, int b, float* __restrict__ out) {
@@ -262,11 +263,12 @@ __global__ void __launch_bounds__(256) k_fs_level(SynLevel s, int b, float* __re
   const int r0 = blockIdx.y * kTO, c0 = blockIdx.x * kTO;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   fs_tile(s, b, l, r0, c0, sh, acc);
-  const int tx = threadIdx.x % kTO, ty = threadIdx.x / kTO;
   float* ol = out + (size_t)l * s.m1 * s.m2;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    int r = r0 + ty + 8 * q, c = c0 + tx;
+    int il, jc;
+    fs_pos(q, il, jc);
+    int r = r0 + il, c = c0 + jc;
     if (r < s.m1 && c < s.m2) ol[(size_t)r * s.m2 + c] = acc[q];
   }
 }
@@ -284,13 +286,14 @@ __global__ void __launch_bounds__(256) k_fs_final(SynFinal s, float* __restrict_
   const int r0 = blockIdx.y * kTO, c0 = blockIdx.x * kTO;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   for (int b = 0; b < 8; ++b) fs_tile(s.lv[b], b, l, r0, c0, sh, acc);
-  const int tx = threadIdx.x % kTO, ty = threadIdx.x / kTO;
   const size_t N = (size_t)s.n1 * s.n2;
   const float* Wd = s.lv[0].W + (size_t)l * s.lv[0].I + s.dirac_off;
   float* Al = A + (size_t)l * N;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    int r = r0 + ty + 8 * q, c = c0 + tx;
+    int il, jc;
+    fs_pos(q, il, jc);
+    int r = r0 + il, c = c0 + jc;
     if (r < s.n1 && c < s.n2) {
       size_t p = (size_t)r * s.n2 + c;
       float v = acc[q] + Wd[p] * (1.f / 3.f);
