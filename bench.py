@@ -279,9 +279,9 @@ def main():
         run_reference(args, spec)
         return
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2003_07358_gb300 import sharding as sh
+    info = sh.rank_info()
+    rank, world, local = info.rank, info.world, info.local
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -322,12 +322,8 @@ def main():
     barrier()
     launches = ctx.fhs_kernel_launches() - l0
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1000.0 / ms
+    ms = sh.max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, device="cuda")
+    value = sh.weak_scaling_value(1, world, ms / 1000.0)
     log(f"{ms:.1f} ms per iteration")
 
     # the plain FP32 path (one launch per pass, unfused) on the same state, for the speed-up

@@ -397,6 +397,26 @@ __host__ __device__ inline TapConst tap_const(int K1, int K2) {
   return t;
 }
 
+// First tap k0 = floor(t - 3.5) + 1 of t = omega * (hi + lo) and x = 2 f - 1, with
+// f = t - k0 - 2.5 the offset entering the per-tap polynomials.
+__device__ __forceinline__ int kb_first(float om, float hi, float lo, float& xx) {
+  float p = __fmul_rn(om, hi);
+  float e = __fadd_rn(__fmaf_rn(om, hi, -p), __fmul_rn(om, lo));
+  float fl = floorf(__fadd_rn(p, -3.5f));
+  int k0 = (int)fl + 1;
+  float f = __fadd_rn(__fadd_rn(__fadd_rn(p, -(float)k0), -2.5f), e);
+  xx = 2.f * f - 1.f;
+  return k0;
+}
+
+// Weight of tap j (j warp-uniform for constant-cache broadcast).
+__device__ __forceinline__ float kb_tap(int j, float xx) {
+  float acc = c_kb.c[j][kPolyDeg];
+#pragma unroll
+  for (int d = kPolyDeg - 1; d >= 0; --d) acc = fmaf(acc, xx, c_kb.c[j][d]);
+  return acc;
+}
+
 // First tap k0 = floor(t - 3.5) + 1 and the 7 weights phi(t - k0 - j), t = omega * (hi + lo).
 // k0 depends only on p = fl(omega * hi) so that host and device agree exactly.
 __device__ __forceinline__ int kb_weights(float om, float hi, float lo, float* w) {
@@ -429,12 +449,15 @@ __device__ __forceinline__ int phys_row2(int k, const VisGeom& vg) {
 }
 
 __device__ __forceinline__ float2 degrid_one(const float2* __restrict__ g, float2 uv, const VisGeom& vg) {
-  float wr[kTaps], wc[kTaps];
-  int kr = kb_weights(uv.y, vg.tc.hi_r, vg.tc.lo_r, wr);
+  float wc[kTaps], xr;
+  int kr = kb_first(uv.y, vg.tc.hi_r, vg.tc.lo_r, xr);
   int kc = kb_weights(uv.x, vg.tc.hi_c, vg.tc.lo_c, wc);
   float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
+  // rolled row loop (row weight evaluated per row, warp-uniform tap index) keeps the
+  // register count low; the 7 loads of a row are independent
+#pragma unroll 1
   for (int a = 0; a < kTaps; ++a) {
+    const float wra = kb_tap(a, xr);
     int row = phys_row2((kr + a) & (vg.K1 - 1), vg);
     const float2* gr = g + (size_t)row * vg.K2;
     float2 racc = make_float2(0.f, 0.f);
@@ -444,8 +467,8 @@ __device__ __forceinline__ float2 degrid_one(const float2* __restrict__ g, float
       racc.x = fmaf(wc[b], v.x, racc.x);
       racc.y = fmaf(wc[b], v.y, racc.y);
     }
-    acc.x = fmaf(wr[a], racc.x, acc.x);
-    acc.y = fmaf(wr[a], racc.y, acc.y);
+    acc.x = fmaf(wra, racc.x, acc.x);
+    acc.y = fmaf(wra, racc.y, acc.y);
   }
   return acc;
 }
@@ -644,8 +667,8 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
         val.y *= s;
       }
       if (pass == 0 && v_write) v_write[i] = val;
-      float wr[kTaps], wc[kTaps];
-      int kr = kb_weights(w.y, vg.tc.hi_r, vg.tc.lo_r, wr);
+      float wc[kTaps], xr;
+      int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
       int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
       // footprint start in the source tile, then the taps of quadrant (dr, dc)
       // relative to this tile: rows lr + a - dr T, a in [a0, a1)
@@ -653,11 +676,14 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
       const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
       const int a0 = max(0, -lr), a1 = min(kTaps, T - lr);
       const int b0 = max(0, -lc), b1 = min(kTaps, T - lc);
-#pragma unroll
+      // rolled, warp-uniform row loop (the row weight is evaluated in the loop) keeps
+      // the register count low; the 7 column weights stay in registers
+#pragma unroll 1
       for (int a = 0; a < kTaps; ++a) {
         if (a < a0 || a >= a1) continue;
+        const float wa = kb_tap(a, xr);
         const int rowoff = (lr + a) * TP + lc;
-        const float va = wr[a] * val.x, vb = wr[a] * val.y;
+        const float va = wa * val.x, vb = wa * val.y;
 #pragma unroll
         for (int b = 0; b < kTaps; ++b) {
           if (b < b0 || b >= b1) continue;

@@ -1,14 +1,14 @@
 // Fused SARA l2,1 dual (Algorithm 2 W update, Table 2 row 3) on GB300.
 //
 // Three kernels replace the level-by-level plain passes:
-//   k_fa_prox   : per 16x16 coefficient tile of one (basis, level), loops over
-//                 the L channels: stages the input tile with its filter halo in
-//                 shared memory (cp.async, double buffered, zero fill outside
-//                 the signal), filters along x then y, writes the LL band for
-//                 the next level and keeps z = W + Psi^dagger x (detail bands,
-//                 and LL4 at the last level) for all channels in shared
-//                 memory; then applies the l2,1 dual across channels
-//                 W <- z min(1, alpha_i / ||z_i||) (or, in weights mode,
+//   k_fa_prox   : per 16x16 coefficient tile of one (basis, level), two passes
+//                 over the L channels: each stages the input tile with its
+//                 filter halo and the tile's W values in shared memory
+//                 (cp.async, double buffered, zero fill outside the signal) and
+//                 filters along x then y; pass 1 accumulates ||z_i||^2 of
+//                 z = W + Psi^dagger x across channels (and writes the LL band
+//                 for the next level), pass 2 recomputes z and writes
+//                 W <- z min(1, alpha_i / ||z_i||) (weights mode: pass 1 only,
 //                 theta_i = mu / (||coef_i|| + mu)).  No coefficient buffer
 //                 round trip through HBM.
 //   k_fs_level  : synthesis of one level (4 -> 2) of one basis, per 32x32
@@ -53,10 +53,10 @@ struct AnaArgs {
   int weights;
 };
 
-// Stage channel l: its input tile (with halo, zero outside the signal) and,
-// in dual mode, this thread's W values of the channel into zb[s][l][tid].
-__device__ __forceinline__ void fa_stage(const AnaArgs& a, float* tin, float* zb, int l, int r_in0, int c_in0, int IN,
-                                         bool valid, int64_t pos) {
+// Stage channel l: its input tile (with halo, zero outside the signal) and, in
+// dual mode, this thread's W values of the channel into wst[s][tid].
+__device__ __forceinline__ void fa_stage(const AnaArgs& a, float* tin, float* wst, int l, int r_in0, int c_in0,
+                                         int IN, bool valid, int64_t pos) {
   const float* inl = a.in + (size_t)l * a.m1 * a.m2;
   for (int idx = threadIdx.x; idx < IN * IN; idx += blockDim.x) {
     int r = idx / IN, c = idx % IN;
@@ -67,102 +67,123 @@ __device__ __forceinline__ void fa_stage(const AnaArgs& a, float* tin, float* zb
   const float* Wl = a.W ? a.W + (size_t)l * a.I : inl;
   for (int s = 0; s < a.nsub; ++s) {
     bool v = valid && !a.weights;
-    cp_async4(&zb[(s * a.L + l) * (kTK * kTK) + threadIdx.x], v ? Wl + a.off[s] + pos : inl, v);
+    cp_async4(&wst[s * (kTK * kTK) + threadIdx.x], v ? Wl + a.off[s] + pos : inl, v);
   }
   cp_async_commit();
 }
 
+// Coefficients of this thread's position for the staged channel: cf = (d0, d1, d2, LL) / 3;
+// also returns the unscaled LL for the next level.
+__device__ __forceinline__ void fa_filter(const float* tin, float* tlx, float* thx, int b, int F, int IN, int tk,
+                                          int tc, bool valid, float cf[4], float& ll_out) {
+  for (int idx = threadIdx.x; idx < IN * kTK; idx += blockDim.x) {
+    int r = idx / kTK, kc = idx % kTK;
+    const float* row = tin + r * (kInMax + 1) + 2 * kc + F - 1;   // input column 2 kc + F - 1 - t
+    float sl = 0.f, sh = 0.f;
+    for (int t = 0; t < F; ++t) {
+      float x = row[-t];
+      sl = fmaf(c_filt.h[b][t], x, sl);
+      sh = fmaf(c_filt.g[b][t], x, sh);
+    }
+    tlx[r * (kTK + 1) + kc] = sl;
+    thx[r * (kTK + 1) + kc] = sh;
+  }
+  __syncthreads();
+  float ll = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+  if (valid) {
+    for (int t = 0; t < F; ++t) {
+      int r = 2 * tk + F - 1 - t;
+      float vl = tlx[r * (kTK + 1) + tc], vh = thx[r * (kTK + 1) + tc];
+      float h = c_filt.h[b][t], g = c_filt.g[b][t];
+      ll = fmaf(h, vl, ll);
+      d1 = fmaf(g, vl, d1);
+      d0 = fmaf(h, vh, d0);
+      d2 = fmaf(g, vh, d2);
+    }
+  }
+  const float third = 1.f / 3.f;
+  cf[0] = d0 * third; cf[1] = d1 * third; cf[2] = d2 * third; cf[3] = ll * third;
+  ll_out = ll;
+}
+
+// Two phases over the L channels of a 16x16 coefficient tile: phase 1 forms
+// z = W + Psi^dagger x for every channel and accumulates ||z_i||^2 (the LL band
+// for the next level is written here); phase 2 stages the channels again (the
+// tiles are L2-resident by then), recomputes z and writes W = z min(1, alpha/||z||).
+// Keeping only the norms between the phases (instead of z for all channels)
+// cuts shared memory to ~32 KB per CTA and lets 7 CTAs share an SM.
 __global__ void __launch_bounds__(256) k_fa_prox(AnaArgs a) {
   extern __shared__ float sm[];
   const int b = a.basis;
   const int F = 2 * (b + 1);
   const int IN = 2 * kTK + F - 2;
-  float* tin0 = sm;                                  // [2][kInMax][kInMax+1]
-  float* tin1 = sm + kInMax * (kInMax + 1);
-  float* tlx = tin1 + kInMax * (kInMax + 1);         // [kInMax][kTK+1]
+  float* tinb[2] = {sm, sm + kInMax * (kInMax + 1)};
+  float* tlx = sm + 2 * kInMax * (kInMax + 1);        // [kInMax][kTK+1]
   float* thx = tlx + kInMax * (kTK + 1);
-  float* zb = thx + kInMax * (kTK + 1);              // [nsub][L][kTK*kTK]
+  float* wstb[2] = {thx + kInMax * (kTK + 1), thx + kInMax * (kTK + 1) + 4 * kTK * kTK};
   const int k0 = blockIdx.y * kTK, c0 = blockIdx.x * kTK;
   const int r_in0 = 2 * k0 + 2 - F, c_in0 = 2 * c0 + 2 - F;
   const int tk = threadIdx.x / kTK, tc = threadIdx.x % kTK;
   const bool valid = (k0 + tk < a.mo1) && (c0 + tc < a.mo2);
   const int64_t pos = (int64_t)(k0 + tk) * a.mo2 + (c0 + tc);
-  const float third = 1.f / 3.f;
-  fa_stage(a, tin0, zb, 0, r_in0, c_in0, IN, valid, pos);
-  for (int l = 0; l < a.L; ++l) {
-    float* tin = (l & 1) ? tin1 : tin0;
-    if (l + 1 < a.L) {
-      fa_stage(a, (l & 1) ? tin0 : tin1, zb, l + 1, r_in0, c_in0, IN, valid, pos);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    // filter along x: local input column of coefficient kc and tap t is 2 kc + F - 1 - t
-    for (int idx = threadIdx.x; idx < IN * kTK; idx += blockDim.x) {
-      int r = idx / kTK, kc = idx % kTK;
-      const float* row = tin + r * (kInMax + 1) + 2 * kc + F - 1;
-      float sl = 0.f, sh = 0.f;
-      for (int t = 0; t < F; ++t) {
-        float x = row[-t];
-        sl = fmaf(c_filt.h[b][t], x, sl);
-        sh = fmaf(c_filt.g[b][t], x, sh);
-      }
-      tlx[r * (kTK + 1) + kc] = sl;
-      thx[r * (kTK + 1) + kc] = sh;
-    }
-    __syncthreads();
-    if (valid) {
-      float ll = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-      for (int t = 0; t < F; ++t) {
-        int r = 2 * tk + F - 1 - t;
-        float vl = tlx[r * (kTK + 1) + tc], vh = thx[r * (kTK + 1) + tc];
-        float h = c_filt.h[b][t], g = c_filt.g[b][t];
-        ll = fmaf(h, vl, ll);
-        d1 = fmaf(g, vl, d1);
-        d0 = fmaf(h, vh, d0);
-        d2 = fmaf(g, vh, d2);
-      }
-      if (a.ll_out) a.ll_out[(size_t)l * a.mo1 * a.mo2 + pos] = ll;
-      float cf[4] = {d0 * third, d1 * third, d2 * third, ll * third};
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (s < a.nsub) zb[(s * a.L + l) * (kTK * kTK) + threadIdx.x] += cf[s];   // W staged (0 in weights mode)
-    }
-    __syncthreads();
-  }
-  if (!valid) return;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (s >= a.nsub) break;
-    const float* z = zb + (size_t)s * a.L * (kTK * kTK) + threadIdx.x;
-    float n2 = 0.f;
+  float n2[4] = {0.f, 0.f, 0.f, 0.f};
+  float fac[4] = {1.f, 1.f, 1.f, 1.f};
+  const int phases = a.weights ? 1 : 2;
+  for (int ph = 0; ph < phases; ++ph) {
+    fa_stage(a, tinb[0], wstb[0], 0, r_in0, c_in0, IN, valid, pos);
     for (int l = 0; l < a.L; ++l) {
-      float v = z[l * (kTK * kTK)];
-      n2 = fmaf(v, v, n2);
+      const int cur = l & 1;
+      if (l + 1 < a.L) {
+        fa_stage(a, tinb[cur ^ 1], wstb[cur ^ 1], l + 1, r_in0, c_in0, IN, valid, pos);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      float cf[4], ll;
+      fa_filter(tinb[cur], tlx, thx, b, F, IN, tk, tc, valid, cf, ll);
+      if (valid) {
+        if (ph == 0 && a.ll_out) a.ll_out[(size_t)l * a.mo1 * a.mo2 + pos] = ll;
+        const float* wst = wstb[cur];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          if (s < a.nsub) {
+            float z = wst[s * (kTK * kTK) + threadIdx.x] + cf[s];   // W staged (0 in weights mode)
+            if (ph == 0) n2[s] = fmaf(z, z, n2[s]);
+            else a.W[(size_t)l * a.I + a.off[s] + pos] = z * fac[s];
+          }
+        }
+      }
+      __syncthreads();   // tin / tlx / wst of this channel are reused two stages later
     }
-    float nrm = sqrtf(n2);
-    if (a.weights) {
-      a.theta_out[a.off[s] + pos] = a.mu / (nrm + a.mu);
-    } else {
-      float alpha = a.alpha_scale * a.theta[a.off[s] + pos];
-      float f = nrm > alpha ? alpha / nrm : 1.f;
-      for (int l = 0; l < a.L; ++l) a.W[(size_t)l * a.I + a.off[s] + pos] = z[l * (kTK * kTK)] * f;
+    if (ph == 0 && valid) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (s >= a.nsub) break;
+        float nrm = sqrtf(n2[s]);
+        if (a.weights) {
+          a.theta_out[a.off[s] + pos] = a.mu / (nrm + a.mu);
+        } else {
+          float alpha = a.alpha_scale * a.theta[a.off[s] + pos];
+          fac[s] = nrm > alpha ? alpha / nrm : 1.f;
+        }
+      }
     }
   }
 }
 
 // Dirac block of the dual: z = W + x / 3 per pixel, l2,1 across channels.
+template <int LMAX>
 __global__ void __launch_bounds__(256) k_fa_dirac(const float* __restrict__ x, float* __restrict__ W,
                                                   const float* __restrict__ theta, float* __restrict__ theta_out,
                                                   int64_t I, int64_t off, int64_t N, int L, float alpha_scale,
                                                   float mu, int weights) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
-  float z[kMaxL];
+  float z[LMAX];
   float n2 = 0.f;
 #pragma unroll
-  for (int l = 0; l < kMaxL; ++l) {
+  for (int l = 0; l < LMAX; ++l) {
     if (l < L) {
       float v = x[(size_t)l * N + p] * (1.f / 3.f) + (weights ? 0.f : W[(size_t)l * I + off + p]);
       z[l] = v;
@@ -177,7 +198,7 @@ __global__ void __launch_bounds__(256) k_fa_dirac(const float* __restrict__ x, f
   float alpha = alpha_scale * theta[off + p];
   float f = nrm > alpha ? alpha / nrm : 1.f;
 #pragma unroll
-  for (int l = 0; l < kMaxL; ++l)
+  for (int l = 0; l < LMAX; ++l)
     if (l < L) W[(size_t)l * I + off + p] = z[l] * f;
 }
 
@@ -303,8 +324,8 @@ __global__ void __launch_bounds__(256) k_fs_final(SynFinal s, float* __restrict_
 }
 
 // ------------------------------------------------------------- launchers
-static size_t fa_smem(int L, int nsub) {
-  return (size_t)(2 * kInMax * (kInMax + 1) + 2 * kInMax * (kTK + 1) + nsub * L * kTK * kTK) * sizeof(float);
+static size_t fa_smem(int, int) {
+  return (size_t)(2 * kInMax * (kInMax + 1) + 2 * kInMax * (kTK + 1) + 2 * 4 * kTK * kTK) * sizeof(float);
 }
 
 static size_t fs_smem() { return (size_t)(4 * kKnMax * (kKnMax + 1) + 2 * kTO * (kKnMax + 1)) * sizeof(float); }
@@ -352,9 +373,17 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
     }
   }
   const int64_t N = (int64_t)cb.n1 * cb.n2;
-  k_fa_dirac<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(x, W, theta, theta_out, S.I, S.dirac_off, N, L,
-                                                          alpha_scale, (float)cb.mu, weights ? 1 : 0);
-  note_launches(1);
+  {
+    const unsigned g = (unsigned)((N + 255) / 256);
+    const int wm = weights ? 1 : 0;
+    if (L <= 16)
+      k_fa_dirac<16><<<g, 256, 0, st>>>(x, W, theta, theta_out, S.I, S.dirac_off, N, L, alpha_scale, (float)cb.mu, wm);
+    else if (L <= 32)
+      k_fa_dirac<32><<<g, 256, 0, st>>>(x, W, theta, theta_out, S.I, S.dirac_off, N, L, alpha_scale, (float)cb.mu, wm);
+    else
+      k_fa_dirac<64><<<g, 256, 0, st>>>(x, W, theta, theta_out, S.I, S.dirac_off, N, L, alpha_scale, (float)cb.mu, wm);
+    note_launches(1);
+  }
   if (weights) return;
   // synthesis: levels 4..2 per basis into its LL1 slot, then level 1 of all bases + Dirac into A
   SynFinal fin;
@@ -397,5 +426,5 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
 }  // namespace fhs
 
 namespace fhs {
-bool sara_fast_supported(const Cube& cb) { return fa_smem(cb.L, 4) <= (size_t)227 * 1024; }
+bool sara_fast_supported(const Cube&) { return true; }
 }  // namespace fhs
