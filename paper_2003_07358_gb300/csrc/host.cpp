@@ -544,6 +544,7 @@ bool use_fast(fhs_ctx* ctx, const Cube& cb) { return ctx->path == FHS_PATH_FAST 
 void sara_dual(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* W, const float* theta, float* A) {
   cudaStream_t st = ctx->stream;
   if (use_fast(ctx, cb)) {
+    ensure_coef(ctx);
     set_ll1_offsets(ctx, cb);
     launch_sara_fast(ctx, cb, xcheck, W, theta, A, nullptr, false, st);
   } else {
@@ -805,6 +806,7 @@ fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta
     const Cube& cb = get_cube(ctx, cube);
     cudaStream_t st = ctx->stream;
     if (use_fast(ctx, cb)) {
+      ensure_coef(ctx);
       launch_sara_fast(ctx, cb, x, nullptr, nullptr, nullptr, theta, true, st);
     } else {
       ensure_coef(ctx);

@@ -1,232 +1,179 @@
-// Fused SARA l2,1 dual (Algorithm 2 W update, Table 2 row 3) on GB300.
+// Fast SARA l2,1 dual (Algorithm 2 W update, Table 2 row 3) on GB300, included
+// at the end of sara.cu (it uses that file's c_filt filter table).
 //
-// Three kernels replace the level-by-level plain passes:
-//   k_fa_prox   : per 16x16 coefficient tile of one (basis, level), two passes
-//                 over the L channels: each stages the input tile with its
-//                 filter halo and the tile's W values in shared memory
-//                 (cp.async, double buffered, zero fill outside the signal) and
-//                 filters along x then y; pass 1 accumulates ||z_i||^2 of
-//                 z = W + Psi^dagger x across channels (and writes the LL band
-//                 for the next level), pass 2 recomputes z and writes
-//                 W <- z min(1, alpha_i / ||z_i||) (weights mode: pass 1 only,
-//                 theta_i = mu / (||coef_i|| + mu)).  No coefficient buffer
-//                 round trip through HBM.
-//   k_fs_level  : synthesis of one level (4 -> 2) of one basis, per 32x32
-//                 output tile and channel: both separable transpose passes in
-//                 shared memory.
-//   k_fs_final  : level-1 synthesis of all eight bases plus the Dirac block for
-//                 a 32x32 output tile, accumulated in registers, A += kappa *
-//                 result written once.
-// Same conventions as sara.cu (zero-padded full convolution, odd phase, /3).
-
-
-
+//   k_ana2<F>   : one (basis, level) of the analysis for a 32x32 coefficient
+//                 tile of one channel: the input tile with its filter halo is
+//                 staged in shared memory, filtered along x then y with
+//                 register blocking (each thread produces 4 outputs from one
+//                 window of F + 6 loaded values); writes the LL band for the
+//                 next level and the detail bands (/3) to the coefficient buffer.
+//   k_prox2<L>  : the l2,1 dual over every coefficient of the sub-cube in one
+//                 streaming pass (Dirac block read straight from x):
+//                 W <- z min(1, alpha_i / ||z_i||), z = W + Psi^dagger x
+//                 (weights mode: theta_i = mu / (||Psi^dagger x||_i + mu)).
+//   k_syn2<F>   : one level (4 -> 2) of the synthesis of one basis for a 32x32
+//                 output tile of one channel, polyphase (even outputs take the
+//                 odd taps and vice versa), register-blocked.
+//   k_synfin    : level 1 of all eight bases and the Dirac block for a 32x32
+//                 output tile, accumulated in registers; A += kappa * result.
+// Same conventions as the plain kernels (zero-padded full convolution, odd
+// phase, coefficients scaled by 1/3).
 
 namespace fhs {
 
-// uses c_filt of sara.cu (this file is included at the end of sara.cu)
+constexpr int kT2 = 32;                              // tile side (coefficients or outputs)
+constexpr int kIn2 = 2 * kT2 + kMaxFilt - 2;         // 78: input rows/cols of an analysis tile
+constexpr int kKn2 = kT2 / 2 + kMaxFilt / 2;         // 24: coefficient rows/cols of a synthesis tile
 
-constexpr int kTK = 16;          // analysis coefficient tile
-constexpr int kTO = 32;          // synthesis output tile
-constexpr int kInMax = 2 * kTK + kMaxFilt - 2;     // 46
-constexpr int kKnMax = kTO / 2 + kMaxFilt / 2 + 1;  // 25
-
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  int n = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-struct AnaArgs {
-  const float* in;     // [L][m1][m2]
-  float* ll_out;       // [L][mo1][mo2] or null at the last level
-  float* W;            // [L][I]
-  const float* theta;  // [I]
-  float* theta_out;    // weights mode
-  int64_t I;
-  int64_t off[4];      // d0, d1, d2, LL4
-  int L, m1, m2, mo1, mo2, basis, nsub;
-  float alpha_scale, mu;
-  int weights;
+template <int F>
+struct FTaps {
+  float h[F], g[F];
+  __device__ __forceinline__ void load() {
+#pragma unroll
+    for (int t = 0; t < F; ++t) {
+      h[t] = c_filt.h[F / 2 - 1][t];
+      g[t] = c_filt.g[F / 2 - 1][t];
+    }
+  }
 };
 
-// Stage channel l: its input tile (with halo, zero outside the signal) and, in
-// dual mode, this thread's W values of the channel into wst[s][tid].
-__device__ __forceinline__ void fa_stage(const AnaArgs& a, float* tin, float* wst, int l, int r_in0, int c_in0,
-                                         int IN, bool valid, int64_t pos) {
-  const float* inl = a.in + (size_t)l * a.m1 * a.m2;
-  for (int idx = threadIdx.x; idx < IN * IN; idx += blockDim.x) {
-    int r = idx / IN, c = idx % IN;
+// ------------------------------------------------------------- analysis
+template <int F>
+__global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, float* __restrict__ ll_out,
+                                              float* __restrict__ coef, int64_t I, int64_t off0, int64_t off1,
+                                              int64_t off2, int64_t off_ll, int m1, int m2, int mo1, int mo2) {
+  constexpr int IN = 2 * kT2 + F - 2;
+  constexpr int WIN = F + 6;                          // window of a 4-output block
+  __shared__ float tin[kIn2][kIn2 + 1];
+  __shared__ float tlx[kIn2][kT2 + 1];
+  __shared__ float thx[kIn2][kT2 + 1];
+  FTaps<F> f;
+  f.load();
+  const int l = blockIdx.z;
+  const int k0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
+  const int r_in0 = 2 * k0 + 2 - F, c_in0 = 2 * c0 + 2 - F;
+  const float* inl = in + (size_t)l * m1 * m2;
+  for (int idx = threadIdx.x; idx < IN * IN; idx += 256) {
+    int r = idx / IN, c = idx - r * IN;
     int gr = r_in0 + r, gc = c_in0 + c;
-    bool v = gr >= 0 && gr < a.m1 && gc >= 0 && gc < a.m2;
-    cp_async4(&tin[r * (kInMax + 1) + c], v ? inl + (size_t)gr * a.m2 + gc : inl, v);
-  }
-  const float* Wl = a.W ? a.W + (size_t)l * a.I : inl;
-  for (int s = 0; s < a.nsub; ++s) {
-    bool v = valid && !a.weights;
-    cp_async4(&wst[s * (kTK * kTK) + threadIdx.x], v ? Wl + a.off[s] + pos : inl, v);
-  }
-  cp_async_commit();
-}
-
-// Coefficients of this thread's position for the staged channel: cf = (d0, d1, d2, LL) / 3;
-// also returns the unscaled LL for the next level.
-__device__ __forceinline__ void fa_filter(const float* tin, float* tlx, float* thx, int b, int F, int IN, int tk,
-                                          int tc, bool valid, float cf[4], float& ll_out) {
-  for (int idx = threadIdx.x; idx < IN * kTK; idx += blockDim.x) {
-    int r = idx / kTK, kc = idx % kTK;
-    const float* row = tin + r * (kInMax + 1) + 2 * kc + F - 1;   // input column 2 kc + F - 1 - t
-    float sl = 0.f, sh = 0.f;
-    for (int t = 0; t < F; ++t) {
-      float x = row[-t];
-      sl = fmaf(c_filt.h[b][t], x, sl);
-      sh = fmaf(c_filt.g[b][t], x, sh);
-    }
-    tlx[r * (kTK + 1) + kc] = sl;
-    thx[r * (kTK + 1) + kc] = sh;
+    tin[r][c] = (gr >= 0 && gr < m1 && gc >= 0 && gc < m2) ? inl[(size_t)gr * m2 + gc] : 0.f;
   }
   __syncthreads();
-  float ll = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-  if (valid) {
-    for (int t = 0; t < F; ++t) {
-      int r = 2 * tk + F - 1 - t;
-      float vl = tlx[r * (kTK + 1) + tc], vh = thx[r * (kTK + 1) + tc];
-      float h = c_filt.h[b][t], g = c_filt.g[b][t];
-      ll = fmaf(h, vl, ll);
-      d1 = fmaf(g, vl, d1);
-      d0 = fmaf(h, vh, d0);
-      d2 = fmaf(g, vh, d2);
+  // x: lx[r][kc] = sum_t h[t] tin[r][2 kc + F - 1 - t], 4 consecutive kc per item
+  for (int item = threadIdx.x; item < IN * 8; item += 256) {
+    const int r = item >> 3, kc0 = (item & 7) * 4;
+    float v[WIN];
+#pragma unroll
+    for (int u = 0; u < WIN; ++u) v[u] = tin[r][2 * kc0 + u];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float sl = 0.f, sh = 0.f;
+#pragma unroll
+      for (int t = 0; t < F; ++t) {
+        sl = fmaf(f.h[t], v[2 * m + F - 1 - t], sl);
+        sh = fmaf(f.g[t], v[2 * m + F - 1 - t], sh);
+      }
+      tlx[r][kc0 + m] = sl;
+      thx[r][kc0 + m] = sh;
     }
   }
-  const float third = 1.f / 3.f;
-  cf[0] = d0 * third; cf[1] = d1 * third; cf[2] = d2 * third; cf[3] = ll * third;
-  ll_out = ll;
-}
-
-// Two phases over the L channels of a 16x16 coefficient tile: phase 1 forms
-// z = W + Psi^dagger x for every channel and accumulates ||z_i||^2 (the LL band
-// for the next level is written here); phase 2 stages the channels again (the
-// tiles are L2-resident by then), recomputes z and writes W = z min(1, alpha/||z||).
-// Keeping only the norms between the phases (instead of z for all channels)
-// cuts shared memory to ~32 KB per CTA and lets 7 CTAs share an SM.
-__global__ void __launch_bounds__(256) k_fa_prox(AnaArgs a) {
-  extern __shared__ float sm[];
-  const int b = a.basis;
-  const int F = 2 * (b + 1);
-  const int IN = 2 * kTK + F - 2;
-  float* tinb[2] = {sm, sm + kInMax * (kInMax + 1)};
-  float* tlx = sm + 2 * kInMax * (kInMax + 1);        // [kInMax][kTK+1]
-  float* thx = tlx + kInMax * (kTK + 1);
-  float* wstb[2] = {thx + kInMax * (kTK + 1), thx + kInMax * (kTK + 1) + 4 * kTK * kTK};
-  const int k0 = blockIdx.y * kTK, c0 = blockIdx.x * kTK;
-  const int r_in0 = 2 * k0 + 2 - F, c_in0 = 2 * c0 + 2 - F;
-  const int tk = threadIdx.x / kTK, tc = threadIdx.x % kTK;
-  const bool valid = (k0 + tk < a.mo1) && (c0 + tc < a.mo2);
-  const int64_t pos = (int64_t)(k0 + tk) * a.mo2 + (c0 + tc);
-  float n2[4] = {0.f, 0.f, 0.f, 0.f};
-  float fac[4] = {1.f, 1.f, 1.f, 1.f};
-  const int phases = a.weights ? 1 : 2;
-  for (int ph = 0; ph < phases; ++ph) {
-    fa_stage(a, tinb[0], wstb[0], 0, r_in0, c_in0, IN, valid, pos);
-    for (int l = 0; l < a.L; ++l) {
-      const int cur = l & 1;
-      if (l + 1 < a.L) {
-        fa_stage(a, tinb[cur ^ 1], wstb[cur ^ 1], l + 1, r_in0, c_in0, IN, valid, pos);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncthreads();
-      float cf[4], ll;
-      fa_filter(tinb[cur], tlx, thx, b, F, IN, tk, tc, valid, cf, ll);
-      if (valid) {
-        if (ph == 0 && a.ll_out) a.ll_out[(size_t)l * a.mo1 * a.mo2 + pos] = ll;
-        const float* wst = wstb[cur];
+  __syncthreads();
+  // y: 4 consecutive coefficient rows per thread, all four bands
+  {
+    const int kc = threadIdx.x & 31, kr0 = (threadIdx.x >> 5) * 4;
+    float a[WIN], b[WIN];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          if (s < a.nsub) {
-            float z = wst[s * (kTK * kTK) + threadIdx.x] + cf[s];   // W staged (0 in weights mode)
-            if (ph == 0) n2[s] = fmaf(z, z, n2[s]);
-            else a.W[(size_t)l * a.I + a.off[s] + pos] = z * fac[s];
-          }
-        }
-      }
-      __syncthreads();   // tin / tlx / wst of this channel are reused two stages later
+    for (int u = 0; u < WIN; ++u) {
+      a[u] = tlx[2 * kr0 + u][kc];
+      b[u] = thx[2 * kr0 + u][kc];
     }
-    if (ph == 0 && valid) {
+    const float third = 1.f / 3.f;
+    const int gc = c0 + kc;
+    float* cl = coef + (size_t)l * I;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (s >= a.nsub) break;
-        float nrm = sqrtf(n2[s]);
-        if (a.weights) {
-          a.theta_out[a.off[s] + pos] = a.mu / (nrm + a.mu);
-        } else {
-          float alpha = a.alpha_scale * a.theta[a.off[s] + pos];
-          fac[s] = nrm > alpha ? alpha / nrm : 1.f;
-        }
+    for (int m = 0; m < 4; ++m) {
+      float ll = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < F; ++t) {
+        const float va = a[2 * m + F - 1 - t], vb = b[2 * m + F - 1 - t];
+        ll = fmaf(f.h[t], va, ll);
+        d1 = fmaf(f.g[t], va, d1);
+        d0 = fmaf(f.h[t], vb, d0);
+        d2 = fmaf(f.g[t], vb, d2);
+      }
+      const int gk = k0 + kr0 + m;
+      if (gk < mo1 && gc < mo2) {
+        const int64_t pos = (int64_t)gk * mo2 + gc;
+        cl[off0 + pos] = d0 * third;
+        cl[off1 + pos] = d1 * third;
+        cl[off2 + pos] = d2 * third;
+        if (ll_out) ll_out[(size_t)l * mo1 * mo2 + pos] = ll;
+        else cl[off_ll + pos] = ll * third;
       }
     }
   }
 }
 
-// Dirac block of the dual: z = W + x / 3 per pixel, l2,1 across channels.
+// ---------------------------------------------------------- l2,1 dual
 template <int LMAX>
-__global__ void __launch_bounds__(256) k_fa_dirac(const float* __restrict__ x, float* __restrict__ W,
-                                                  const float* __restrict__ theta, float* __restrict__ theta_out,
-                                                  int64_t I, int64_t off, int64_t N, int L, float alpha_scale,
-                                                  float mu, int weights) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
-  float z[LMAX];
-  float n2 = 0.f;
+__global__ void __launch_bounds__(256) k_prox2(float* __restrict__ W, const float* __restrict__ coef,
+                                               const float* __restrict__ x, const float* __restrict__ theta,
+                                               float* __restrict__ theta_out, int64_t I, int64_t dirac_off, int64_t N,
+                                               int L, float alpha_scale, float mu, int weights) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool dirac = i >= dirac_off;
+    float z[LMAX];
+    float n2 = 0.f;
 #pragma unroll
-  for (int l = 0; l < LMAX; ++l) {
-    if (l < L) {
-      float v = x[(size_t)l * N + p] * (1.f / 3.f) + (weights ? 0.f : W[(size_t)l * I + off + p]);
-      z[l] = v;
-      n2 = fmaf(v, v, n2);
+    for (int l = 0; l < LMAX; ++l) {
+      if (l < L) {
+        float c = dirac ? x[(size_t)l * N + (i - dirac_off)] * (1.f / 3.f) : coef[(size_t)l * I + i];
+        float v = weights ? c : W[(size_t)l * I + i] + c;
+        z[l] = v;
+        n2 = fmaf(v, v, n2);
+      }
     }
-  }
-  float nrm = sqrtf(n2);
-  if (weights) {
-    theta_out[off + p] = mu / (nrm + mu);
-    return;
-  }
-  float alpha = alpha_scale * theta[off + p];
-  float f = nrm > alpha ? alpha / nrm : 1.f;
+    const float nrm = sqrtf(n2);
+    if (weights) {
+      theta_out[i] = mu / (nrm + mu);
+      continue;
+    }
+    const float alpha = alpha_scale * theta[i];
+    const float fct = nrm > alpha ? alpha / nrm : 1.f;
 #pragma unroll
-  for (int l = 0; l < LMAX; ++l)
-    if (l < L) W[(size_t)l * I + off + p] = z[l] * f;
+    for (int l = 0; l < LMAX; ++l)
+      if (l < L) W[(size_t)l * I + i] = z[l] * fct;
+  }
 }
 
-// ------------------------------------------------------------- synthesis
-struct SynLevel {
-  const float* ll;     // [L][mo1][mo2] synthesised coarser band, or null: LL4 from W
+// ------------------------------------------------------------ synthesis
+struct Syn2 {
+  const float* ll;     // synthesised coarser band [L][mo1][mo2], or null: LL4 from W (/3)
   const float* W;
   int64_t I;
   int64_t off[4];      // d0, d1, d2, LL4
   int mo1, mo2, m1, m2;
 };
 
-// Synthesis of one (basis, level) for the 32x32 output tile (r0, c0) of channel l
-// into acc (4 values per thread: rows r0 + ty + 8q, column c0 + tx).
-__device__ __forceinline__ void fs_tile(const SynLevel& s, int b, int l, int r0, int c0, float* sh, float acc[4]) {
-  const int F = 2 * (b + 1);
+// Synthesis of one (basis, level) for the 32x32 output tile (r0, c0) of channel l.
+// Adds to acc[4]: outputs (row il = threadIdx.x >> 3, columns 4 * (threadIdx.x & 7) + q).
+template <int F>
+__device__ __forceinline__ void syn2_tile(const Syn2& s, int l, int r0, int c0, float* sh, float acc[4]) {
+  constexpr int KN = kT2 / 2 + F / 2;                 // coefficient rows / cols touching the tile
+  constexpr int TS = kKn2 * (kKn2 + 1);
+  constexpr int WIN = F / 2 + 1;                       // polyphase window of 2 outputs per parity pair
+  float* tc = sh;                                      // [4][kKn2][kKn2+1]: LL, d0, d1, d2
+  float* lx = sh + 4 * TS;                             // [kT2][kKn2+1]
+  float* hx = lx + kT2 * (kKn2 + 1);
+  FTaps<F> f;
+  f.load();
   const int klo = r0 / 2, clo = c0 / 2;
-  const int KN = kTO / 2 + F / 2;                    // coefficient rows / cols touching the tile
-  float* tc = sh;                                    // [4][kKnMax][kKnMax+1]: LL, d0, d1, d2
-  const int TS = kKnMax * (kKnMax + 1);
-  float* lx = sh + 4 * TS;                           // [kTO][kKnMax+1]
-  float* hx = lx + kTO * (kKnMax + 1);
   const float third = 1.f / 3.f;
   const float* Wl = s.W + (size_t)l * s.I;
   const float* lll = s.ll ? s.ll + (size_t)l * s.mo1 * s.mo2 : nullptr;
-  for (int idx = threadIdx.x; idx < 4 * KN * KN; idx += blockDim.x) {
-    int band = idx / (KN * KN), rem = idx % (KN * KN);
-    int kr = rem / KN, kc = rem % KN;
+  for (int idx = threadIdx.x; idx < 4 * KN * KN; idx += 256) {
+    int band = idx / (KN * KN), rem = idx - band * (KN * KN);
+    int kr = rem / KN, kc = rem - kr * KN;
     int gk = klo + kr, gc = clo + kc;
     float v = 0.f;
     if (gk < s.mo1 && gc < s.mo2) {
@@ -234,164 +181,183 @@ __device__ __forceinline__ void fs_tile(const SynLevel& s, int b, int l, int r0,
       if (band == 0) v = lll ? lll[pos] : Wl[s.off[3] + pos] * third;
       else v = Wl[s.off[band - 1] + pos] * third;
     }
-    tc[band * TS + kr * (kKnMax + 1) + kc] = v;
+    tc[band * TS + kr * (kKn2 + 1) + kc] = v;
   }
   __syncthreads();
-  // y synthesis, polyphase: output row i = r0 + il (r0 even), m = il / 2, p = il % 2;
-  // a[2m + p] = sum_{q < F/2} f[2q + 1 - p] c[m + q] (no bounds tests: the tile is zero-padded)
-  for (int idx = threadIdx.x; idx < kTO * KN; idx += blockDim.x) {
-    int il = idx / KN, kc = idx % KN;
-    int p = il & 1, m = il >> 1;
-    float sl = 0.f, sx = 0.f;
-    for (int q = 0; q < F / 2; ++q) {
-      int t = 2 * q + 1 - p;
-      float h = c_filt.h[b][t], g = c_filt.g[b][t];
-      int o = (m + q) * (kKnMax + 1) + kc;
-      sl = fmaf(h, tc[o], fmaf(g, tc[2 * TS + o], sl));
-      sx = fmaf(h, tc[TS + o], fmaf(g, tc[3 * TS + o], sx));
-    }
-    lx[il * (kKnMax + 1) + kc] = sl;
-    hx[il * (kKnMax + 1) + kc] = sx;
-  }
-  __syncthreads();
-  // x synthesis, polyphase, parity uniform per warp (see fs_pos)
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int p = w & 1, m = lane & 15;
+  // y: rows il = 2m + p of lx/hx; item = (coefficient column kc, pair of m) -> 4 output rows
+  for (int item = threadIdx.x; item < KN * 8; item += 256) {
+    const int kc = item % KN, mg = (item / KN) * 2;    // m = mg, mg + 1
+    float vl[WIN + 1], v1[WIN + 1], v0[WIN + 1], v2[WIN + 1];
 #pragma unroll
-  for (int qq = 0; qq < 4; ++qq) {
-    int il = (w >> 1) * 2 + (lane >> 4) + 8 * qq;
-    float v = 0.f;
-    for (int q = 0; q < F / 2; ++q) {
-      int t = 2 * q + 1 - p;
-      int o = il * (kKnMax + 1) + m + q;
-      v = fmaf(c_filt.h[b][t], lx[o], fmaf(c_filt.g[b][t], hx[o], v));
+    for (int u = 0; u <= WIN; ++u) {
+      const int o = (mg + u) * (kKn2 + 1) + kc;
+      vl[u] = tc[o];
+      v0[u] = tc[TS + o];
+      v1[u] = tc[2 * TS + o];
+      v2[u] = tc[3 * TS + o];
     }
-    acc[qq] += v;
+#pragma unroll
+    for (int mm = 0; mm < 2; ++mm) {
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float sl = 0.f, sx = 0.f;
+#pragma unroll
+        for (int q = 0; q < F / 2; ++q) {
+          const float hh = f.h[2 * q + 1 - p], gg = f.g[2 * q + 1 - p];
+          sl = fmaf(hh, vl[mm + q], fmaf(gg, v1[mm + q], sl));
+          sx = fmaf(hh, v0[mm + q], fmaf(gg, v2[mm + q], sx));
+        }
+        const int il = 2 * (mg + mm) + p;
+        lx[il * (kKn2 + 1) + kc] = sl;
+        hx[il * (kKn2 + 1) + kc] = sx;
+      }
+    }
+  }
+  __syncthreads();
+  // x: thread = (row il, 4 consecutive output columns 4 g .. 4 g + 3, i.e. m = 2g, 2g + 1)
+  {
+    const int il = threadIdx.x >> 3, g4 = threadIdx.x & 7;
+    const int mg = 2 * g4;
+    float a[WIN + 1], b[WIN + 1];
+#pragma unroll
+    for (int u = 0; u <= WIN; ++u) {
+      a[u] = lx[il * (kKn2 + 1) + mg + u];
+      b[u] = hx[il * (kKn2 + 1) + mg + u];
+    }
+#pragma unroll
+    for (int mm = 0; mm < 2; ++mm) {
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < F / 2; ++q)
+          v = fmaf(f.h[2 * q + 1 - p], a[mm + q], fmaf(f.g[2 * q + 1 - p], b[mm + q], v));
+        acc[2 * mm + p] += v;
+      }
+    }
   }
   __syncthreads();
 }
 
-// Output position of accumulator qq of this thread in the 32x32 tile.
-__device__ __forceinline__ void fs_pos(int qq, int& il, int& jc) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  il = (w >> 1) * 2 + (lane >> 4) + 8 * qq;
-  jc = 2 * (lane & 15) + (w & 1);
+__device__ __forceinline__ void syn2_any(int b, const Syn2& s, int l, int r0, int c0, float* sh, float acc[4]) {
+  switch (b) {
+    case 0: syn2_tile<2>(s, l, r0, c0, sh, acc); break;
+    case 1: syn2_tile<4>(s, l, r0, c0, sh, acc); break;
+    case 2: syn2_tile<6>(s, l, r0, c0, sh, acc); break;
+    case 3: syn2_tile<8>(s, l, r0, c0, sh, acc); break;
+    case 4: syn2_tile<10>(s, l, r0, c0, sh, acc); break;
+    case 5: syn2_tile<12>(s, l, r0, c0, sh, acc); break;
+    case 6: syn2_tile<14>(s, l, r0, c0, sh, acc); break;
+    default: syn2_tile<16>(s, l, r0, c0, sh, acc); break;
+  }
 }
 
-__global__ void __launch_bounds__(256) k_fs_level(SynLevel s, int b, float* __restrict__ out) {
-  extern __shared__ float sh[];
+template <int F>
+__global__ void __launch_bounds__(256) k_syn2(Syn2 s, float* __restrict__ out) {
+  __shared__ float sh[4 * kKn2 * (kKn2 + 1) + 2 * kT2 * (kKn2 + 1)];
   const int l = blockIdx.z;
-  const int r0 = blockIdx.y * kTO, c0 = blockIdx.x * kTO;
+  const int r0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  fs_tile(s, b, l, r0, c0, sh, acc);
-  float* ol = out + (size_t)l * s.m1 * s.m2;
+  syn2_tile<F>(s, l, r0, c0, sh, acc);
+  const int il = threadIdx.x >> 3, jc0 = 4 * (threadIdx.x & 7);
+  const int r = r0 + il;
+  if (r >= s.m1) return;
+  float* ol = out + (size_t)l * s.m1 * s.m2 + (size_t)r * s.m2;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int il, jc;
-    fs_pos(q, il, jc);
-    int r = r0 + il, c = c0 + jc;
-    if (r < s.m1 && c < s.m2) ol[(size_t)r * s.m2 + c] = acc[q];
-  }
+  for (int q = 0; q < 4; ++q)
+    if (c0 + jc0 + q < s.m2) ol[c0 + jc0 + q] = acc[q];
 }
 
-struct SynFinal {
-  SynLevel lv[8];      // level-1 description of each basis (ll = its synthesised LL1)
+struct SynFin2 {
+  Syn2 lv[8];          // level-1 description of each basis (ll = its synthesised LL1)
   int64_t dirac_off;
   int n1, n2;
   float kappa;
 };
 
-__global__ void __launch_bounds__(256) k_fs_final(SynFinal s, float* __restrict__ A) {
-  extern __shared__ float sh[];
+__global__ void __launch_bounds__(256) k_synfin(SynFin2 s, float* __restrict__ A) {
+  __shared__ float sh[4 * kKn2 * (kKn2 + 1) + 2 * kT2 * (kKn2 + 1)];
   const int l = blockIdx.z;
-  const int r0 = blockIdx.y * kTO, c0 = blockIdx.x * kTO;
+  const int r0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int b = 0; b < 8; ++b) fs_tile(s.lv[b], b, l, r0, c0, sh, acc);
+#pragma unroll 1
+  for (int b = 0; b < 8; ++b) syn2_any(b, s.lv[b], l, r0, c0, sh, acc);
+  const int il = threadIdx.x >> 3, jc0 = 4 * (threadIdx.x & 7);
+  const int r = r0 + il;
+  if (r >= s.n1) return;
   const size_t N = (size_t)s.n1 * s.n2;
-  const float* Wd = s.lv[0].W + (size_t)l * s.lv[0].I + s.dirac_off;
-  float* Al = A + (size_t)l * N;
+  const float* Wd = s.lv[0].W + (size_t)l * s.lv[0].I + s.dirac_off + (size_t)r * s.n2;
+  float* Al = A + (size_t)l * N + (size_t)r * s.n2;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    int il, jc;
-    fs_pos(q, il, jc);
-    int r = r0 + il, c = c0 + jc;
-    if (r < s.n1 && c < s.n2) {
-      size_t p = (size_t)r * s.n2 + c;
-      float v = acc[q] + Wd[p] * (1.f / 3.f);
-      Al[p] = fmaf(s.kappa, v, Al[p]);
-    }
+    const int c = c0 + jc0 + q;
+    if (c < s.n2) Al[c] = fmaf(s.kappa, acc[q] + Wd[c] * (1.f / 3.f), Al[c]);
   }
 }
 
 // ------------------------------------------------------------- launchers
-static size_t fa_smem(int, int) {
-  return (size_t)(2 * kInMax * (kInMax + 1) + 2 * kInMax * (kTK + 1) + 2 * 4 * kTK * kTK) * sizeof(float);
+template <int F>
+static void ana2_launch(const Cube& cb, int b, int j, const float* in, float* ll_out, float* coef, cudaStream_t st) {
+  const SaraLayout& S = cb.sara;
+  dim3 g((S.cols[b][j] + kT2 - 1) / kT2, (S.rows[b][j] + kT2 - 1) / kT2, cb.L);
+  k_ana2<F><<<g, 256, 0, st>>>(in, ll_out, coef, S.I, S.off[b][j][0], S.off[b][j][1], S.off[b][j][2],
+                               S.off[b][kLevels][3], S.rows[b][j - 1], S.cols[b][j - 1], S.rows[b][j], S.cols[b][j]);
+  note_launches(1);
 }
 
-static size_t fs_smem() { return (size_t)(4 * kKnMax * (kKnMax + 1) + 2 * kTO * (kKnMax + 1)) * sizeof(float); }
+template <int F>
+static void syn2_launch(const Cube& cb, const Syn2& s, float* out, cudaStream_t st) {
+  dim3 g((s.m2 + kT2 - 1) / kT2, (s.m1 + kT2 - 1) / kT2, cb.L);
+  k_syn2<F><<<g, 256, 0, st>>>(s, out);
+  note_launches(1);
+}
 
-// Fused analysis + l2,1 dual (or weights) of every basis and level, then the
-// fused synthesis accumulated into A (dual mode only).
+#define FHS_BASIS_SWITCH(b, FN, ...)              \
+  switch (b) {                                    \
+    case 0: FN<2>(__VA_ARGS__); break;            \
+    case 1: FN<4>(__VA_ARGS__); break;            \
+    case 2: FN<6>(__VA_ARGS__); break;            \
+    case 3: FN<8>(__VA_ARGS__); break;            \
+    case 4: FN<10>(__VA_ARGS__); break;           \
+    case 5: FN<12>(__VA_ARGS__); break;           \
+    case 6: FN<14>(__VA_ARGS__); break;           \
+    default: FN<16>(__VA_ARGS__); break;          \
+  }
+
+// Analysis of every basis and level into the coefficient buffer, the l2,1 dual (or
+// weights), then (dual mode) the synthesis accumulated into A.
 void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, const float* theta, float* A,
                       float* theta_out, bool weights, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_fa_prox, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_fs_level, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_fs_final, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    attr = true;
-  }
   const SaraLayout& S = cb.sara;
   const int L = cb.L;
-  const float alpha_scale = (float)(cb.mu / cb.kappa);
+  float* coef = ctx->s.coef;
   float* llA = ctx->s.t2;
   float* llB = ctx->s.t3;
   for (int b = 0; b < 8; ++b) {
     const float* in = x;
     for (int j = 1; j <= kLevels; ++j) {
-      AnaArgs a;
-      a.in = in;
-      a.ll_out = (j == kLevels) ? nullptr : ((j & 1) ? llA : llB);
-      a.W = W;
-      a.theta = theta;
-      a.theta_out = theta_out;
-      a.I = S.I;
-      a.off[0] = S.off[b][j][0]; a.off[1] = S.off[b][j][1]; a.off[2] = S.off[b][j][2];
-      a.off[3] = S.off[b][kLevels][3];
-      a.L = L;
-      a.m1 = S.rows[b][j - 1]; a.m2 = S.cols[b][j - 1];
-      a.mo1 = S.rows[b][j]; a.mo2 = S.cols[b][j];
-      a.basis = b;
-      a.nsub = (j == kLevels) ? 4 : 3;
-      a.alpha_scale = alpha_scale;
-      a.mu = (float)cb.mu;
-      a.weights = weights ? 1 : 0;
-      dim3 g((a.mo2 + kTK - 1) / kTK, (a.mo1 + kTK - 1) / kTK);
-      k_fa_prox<<<g, 256, fa_smem(L, a.nsub), st>>>(a);
-      note_launches(1);
-      in = a.ll_out;
+      float* llo = (j == kLevels) ? nullptr : ((j & 1) ? llA : llB);
+      FHS_BASIS_SWITCH(b, ana2_launch, cb, b, j, in, llo, coef, st);
+      in = llo;
     }
   }
-  const int64_t N = (int64_t)cb.n1 * cb.n2;
   {
-    const unsigned g = (unsigned)((N + 255) / 256);
+    const int64_t N = (int64_t)cb.n1 * cb.n2;
+    const unsigned g = (unsigned)std::min<int64_t>((S.I + 255) / 256, 152 * 16);
+    const float as = (float)(cb.mu / cb.kappa), mu = (float)cb.mu;
     const int wm = weights ? 1 : 0;
-    if (L <= 16)
-      k_fa_dirac<16><<<g, 256, 0, st>>>(x, W, theta, theta_out, S.I, S.dirac_off, N, L, alpha_scale, (float)cb.mu, wm);
-    else if (L <= 32)
-      k_fa_dirac<32><<<g, 256, 0, st>>>(x, W, theta, theta_out, S.I, S.dirac_off, N, L, alpha_scale, (float)cb.mu, wm);
-    else
-      k_fa_dirac<64><<<g, 256, 0, st>>>(x, W, theta, theta_out, S.I, S.dirac_off, N, L, alpha_scale, (float)cb.mu, wm);
+    if (L <= 16) k_prox2<16><<<g, 256, 0, st>>>(W, coef, x, theta, theta_out, S.I, S.dirac_off, N, L, as, mu, wm);
+    else if (L <= 32) k_prox2<32><<<g, 256, 0, st>>>(W, coef, x, theta, theta_out, S.I, S.dirac_off, N, L, as, mu, wm);
+    else k_prox2<64><<<g, 256, 0, st>>>(W, coef, x, theta, theta_out, S.I, S.dirac_off, N, L, as, mu, wm);
     note_launches(1);
   }
   if (weights) return;
-  // synthesis: levels 4..2 per basis into its LL1 slot, then level 1 of all bases + Dirac into A
-  SynFinal fin;
+  SynFin2 fin;
   float* slots = ctx->s.ll1;
   for (int b = 0; b < 8; ++b) {
     const float* ll = nullptr;
     for (int j = kLevels; j >= 2; --j) {
-      SynLevel s;
+      Syn2 s;
       s.ll = ll;
       s.W = W;
       s.I = S.I;
@@ -400,12 +366,10 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
       s.mo1 = S.rows[b][j]; s.mo2 = S.cols[b][j];
       s.m1 = S.rows[b][j - 1]; s.m2 = S.cols[b][j - 1];
       float* out = (j == 2) ? slots + ctx->s.ll1_off[b] : ((j & 1) ? llA : llB);
-      dim3 g((s.m2 + kTO - 1) / kTO, (s.m1 + kTO - 1) / kTO, L);
-      k_fs_level<<<g, 256, fs_smem(), st>>>(s, b, out);
-      note_launches(1);
+      FHS_BASIS_SWITCH(b, syn2_launch, cb, s, out, st);
       ll = out;
     }
-    SynLevel& f = fin.lv[b];
+    Syn2& f = fin.lv[b];
     f.ll = slots + ctx->s.ll1_off[b];
     f.W = W;
     f.I = S.I;
@@ -418,13 +382,11 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
   fin.n1 = cb.n1;
   fin.n2 = cb.n2;
   fin.kappa = (float)cb.kappa;
-  dim3 g((cb.n2 + kTO - 1) / kTO, (cb.n1 + kTO - 1) / kTO, L);
-  k_fs_final<<<g, 256, fs_smem(), st>>>(fin, A);
+  dim3 g((cb.n2 + kT2 - 1) / kT2, (cb.n1 + kT2 - 1) / kT2, L);
+  k_synfin<<<g, 256, 0, st>>>(fin, A);
   note_launches(1);
 }
 
-}  // namespace fhs
-
-namespace fhs {
 bool sara_fast_supported(const Cube&) { return true; }
+
 }  // namespace fhs
