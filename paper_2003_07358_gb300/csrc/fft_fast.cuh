@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(Row2Cfg<N>::NT) k_row2(float2* __restrict__ gr
   const int r0 = blockIdx.x * S;
   float2* gl = grid + (size_t)l * K1 * N;
   const int h2 = n2 / 2;
+#pragma unroll
   for (int idx = threadIdx.x; idx < N * S; idx += NT) {
     int s = idx / N, n = idx % N;
     bool in = n < h2 || n >= N - h2;
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(Row2Cfg<N>::NT) k_row2(float2* __restrict__ gr
   }
   __syncthreads();
   smem_fft<N, S, NT, true, true>(smem, tw, twstride, inv != 0);
+#pragma unroll
   for (int idx = threadIdx.x; idx < N * S; idx += NT) {
     int s = idx / N, n = idx % N;
     bool in = n < h2 || n >= N - h2;
@@ -63,6 +65,7 @@ __global__ void __launch_bounds__(ColCfg<N>::NT) k_colA_fwd(const float* __restr
   const int l = blockIdx.z, g = blockIdx.y, c0 = blockIdx.x * W;
   const float* xl = x + (size_t)l * n1 * n2;
   const int h1 = n1 / 2, h2 = n2 / 2;
+#pragma unroll
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     int i = idx / W, w = idx % W;
     int cc = c0 + w;
@@ -78,6 +81,7 @@ __global__ void __launch_bounds__(ColCfg<N>::NT) k_colA_fwd(const float* __restr
   __syncthreads();
   smem_fft<N, W, NT>(smem, tw, twN, false);
   float2* gl = grid + (size_t)l * K1 * K2;
+#pragma unroll
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     int i = idx / W, w = idx % W;
     int cc = c0 + w;
@@ -96,6 +100,7 @@ __global__ void __launch_bounds__(ColCfg<N>::NT) k_colB(float2* __restrict__ gri
   extern __shared__ float2 smem[];
   const int l = blockIdx.z, k1 = blockIdx.y, c0 = blockIdx.x * W;
   float2* gl = grid + (size_t)l * K1 * K2 + (size_t)N * k1 * K2;
+#pragma unroll
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     int i = idx / W, w = idx % W;
     int cc = c0 + w;
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(ColCfg<N>::NT) k_colB(float2* __restrict__ gri
   }
   __syncthreads();
   smem_fft<N, W, NT>(smem, tw, twN, inv != 0);
+#pragma unroll
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     int i = idx / W, w = idx % W;
     int cc = c0 + w;
@@ -122,6 +128,7 @@ __global__ void __launch_bounds__(ColCfg<N>::NT) k_colA_adj(const float2* __rest
   extern __shared__ float2 smem[];
   const int l = blockIdx.z, g = blockIdx.y, c0 = blockIdx.x * W;
   const float2* gl = grid + (size_t)l * K1 * K2;
+#pragma unroll
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     int i = idx / W, w = idx % W;
     int cc = c0 + w;
@@ -137,6 +144,7 @@ __global__ void __launch_bounds__(ColCfg<N>::NT) k_colA_adj(const float2* __rest
   const float e = eta ? eta[l] : 1.f;
   const int h1 = n1 / 2, h2 = n2 / 2;
   float* ol = out + (size_t)l * n1 * n2;
+#pragma unroll
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     int i = idx / W, w = idx % W;
     int cc = c0 + w;

@@ -115,34 +115,52 @@ __global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, floa
 }
 
 // ---------------------------------------------------------- l2,1 dual
+// Each warp takes 64 consecutive coefficients (two per lane, 32 apart), so every
+// channel plane is read in 256-byte runs: better DRAM page locality than one
+// coefficient per lane across 2L planes.
 template <int LMAX>
 __global__ void __launch_bounds__(256) k_prox2(float* __restrict__ W, const float* __restrict__ coef,
                                                const float* __restrict__ x, const float* __restrict__ theta,
                                                float* __restrict__ theta_out, int64_t I, int64_t dirac_off, int64_t N,
                                                int L, float alpha_scale, float mu, int weights) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
-    const bool dirac = i >= dirac_off;
-    float z[LMAX];
-    float n2 = 0.f;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 64; base < I; base += nwarps * 64) {
+    int64_t ii[2] = {base + lane, base + 32 + lane};
+    float z[2][LMAX];
+    float n2[2] = {0.f, 0.f};
 #pragma unroll
     for (int l = 0; l < LMAX; ++l) {
       if (l < L) {
-        float c = dirac ? x[(size_t)l * N + (i - dirac_off)] * (1.f / 3.f) : coef[(size_t)l * I + i];
-        float v = weights ? c : W[(size_t)l * I + i] + c;
-        z[l] = v;
-        n2 = fmaf(v, v, n2);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int64_t i = ii[k];
+          float v = 0.f;
+          if (i < I) {
+            float c = i >= dirac_off ? x[(size_t)l * N + (i - dirac_off)] * (1.f / 3.f) : coef[(size_t)l * I + i];
+            v = weights ? c : W[(size_t)l * I + i] + c;
+          }
+          z[k][l] = v;
+          n2[k] = fmaf(v, v, n2[k]);
+        }
       }
     }
-    const float nrm = sqrtf(n2);
-    if (weights) {
-      theta_out[i] = mu / (nrm + mu);
-      continue;
-    }
-    const float alpha = alpha_scale * theta[i];
-    const float fct = nrm > alpha ? alpha / nrm : 1.f;
 #pragma unroll
-    for (int l = 0; l < LMAX; ++l)
-      if (l < L) W[(size_t)l * I + i] = z[l] * fct;
+    for (int k = 0; k < 2; ++k) {
+      const int64_t i = ii[k];
+      if (i >= I) continue;
+      const float nrm = sqrtf(n2[k]);
+      if (weights) {
+        theta_out[i] = mu / (nrm + mu);
+        continue;
+      }
+      const float alpha = alpha_scale * theta[i];
+      const float fct = nrm > alpha ? alpha / nrm : 1.f;
+#pragma unroll
+      for (int l = 0; l < LMAX; ++l)
+        if (l < L) W[(size_t)l * I + i] = z[k][l] * fct;
+    }
   }
 }
 
@@ -155,46 +173,57 @@ struct Syn2 {
   int mo1, mo2, m1, m2;
 };
 
-// Synthesis of one (basis, level) for the 32x32 output tile (r0, c0) of channel l.
-// Adds to acc[4]: outputs (row il = threadIdx.x >> 3, columns 4 * (threadIdx.x & 7) + q).
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+constexpr int kTS2 = kKn2 * (kKn2 + 1);             // one staged band
+
+// Stage the four coefficient bands (LL, d0, d1, d2; raw values, zero outside the
+// level) of the output tile (r0, c0) of channel l into tc[4][kKn2][kKn2+1].
 template <int F>
-__device__ __forceinline__ void syn2_tile(const Syn2& s, int l, int r0, int c0, float* sh, float acc[4]) {
-  constexpr int KN = kT2 / 2 + F / 2;                 // coefficient rows / cols touching the tile
-  constexpr int TS = kKn2 * (kKn2 + 1);
-  constexpr int WIN = F / 2 + 1;                       // polyphase window of 2 outputs per parity pair
-  float* tc = sh;                                      // [4][kKn2][kKn2+1]: LL, d0, d1, d2
-  float* lx = sh + 4 * TS;                             // [kT2][kKn2+1]
-  float* hx = lx + kT2 * (kKn2 + 1);
-  FTaps<F> f;
-  f.load();
+__device__ __forceinline__ void syn2_stage(const Syn2& s, int l, int r0, int c0, float* tc) {
+  constexpr int KN = kT2 / 2 + F / 2;
   const int klo = r0 / 2, clo = c0 / 2;
-  const float third = 1.f / 3.f;
   const float* Wl = s.W + (size_t)l * s.I;
   const float* lll = s.ll ? s.ll + (size_t)l * s.mo1 * s.mo2 : nullptr;
   for (int idx = threadIdx.x; idx < 4 * KN * KN; idx += 256) {
     int band = idx / (KN * KN), rem = idx - band * (KN * KN);
     int kr = rem / KN, kc = rem - kr * KN;
     int gk = klo + kr, gc = clo + kc;
-    float v = 0.f;
-    if (gk < s.mo1 && gc < s.mo2) {
-      int64_t pos = (int64_t)gk * s.mo2 + gc;
-      if (band == 0) v = lll ? lll[pos] : Wl[s.off[3] + pos] * third;
-      else v = Wl[s.off[band - 1] + pos] * third;
-    }
-    tc[band * TS + kr * (kKn2 + 1) + kc] = v;
+    bool v = gk < s.mo1 && gc < s.mo2;
+    int64_t pos = v ? (int64_t)gk * s.mo2 + gc : 0;
+    const float* src = band == 0 ? (lll ? lll + pos : Wl + s.off[3] + pos) : Wl + s.off[band - 1] + pos;
+    cp_async4(&tc[band * kTS2 + kr * (kKn2 + 1) + kc], src, v);
   }
-  __syncthreads();
-  // y: rows il = 2m + p of lx/hx; item = (coefficient column kc, pair of m) -> 4 output rows
+  cp_async_commit();
+}
+
+// Synthesis of one staged (basis, level) tile, added to acc[4]: outputs at row
+// il = threadIdx.x >> 3, columns 4 * (threadIdx.x & 7) + q.  Coefficients carry
+// the 1/3 of the dictionary except a synthesised LL band (ll_scale = 1).
+template <int F>
+__device__ __forceinline__ void syn2_compute(const float* tc, float* lx, float* hx, float ll_scale, float acc[4]) {
+  constexpr int KN = kT2 / 2 + F / 2;
+  constexpr int WIN = F / 2 + 1;
+  FTaps<F> f;
+  f.load();
+  const float third = 1.f / 3.f;
   for (int item = threadIdx.x; item < KN * 8; item += 256) {
-    const int kc = item % KN, mg = (item / KN) * 2;    // m = mg, mg + 1
+    const int kc = item % KN, mg = (item / KN) * 2;
     float vl[WIN + 1], v1[WIN + 1], v0[WIN + 1], v2[WIN + 1];
 #pragma unroll
     for (int u = 0; u <= WIN; ++u) {
       const int o = (mg + u) * (kKn2 + 1) + kc;
-      vl[u] = tc[o];
-      v0[u] = tc[TS + o];
-      v1[u] = tc[2 * TS + o];
-      v2[u] = tc[3 * TS + o];
+      vl[u] = tc[o] * ll_scale;
+      v0[u] = tc[kTS2 + o] * third;
+      v1[u] = tc[2 * kTS2 + o] * third;
+      v2[u] = tc[3 * kTS2 + o] * third;
     }
 #pragma unroll
     for (int mm = 0; mm < 2; ++mm) {
@@ -214,7 +243,6 @@ __device__ __forceinline__ void syn2_tile(const Syn2& s, int l, int r0, int c0, 
     }
   }
   __syncthreads();
-  // x: thread = (row il, 4 consecutive output columns 4 g .. 4 g + 3, i.e. m = 2g, 2g + 1)
   {
     const int il = threadIdx.x >> 3, g4 = threadIdx.x & 7;
     const int mg = 2 * g4;
@@ -239,26 +267,43 @@ __device__ __forceinline__ void syn2_tile(const Syn2& s, int l, int r0, int c0, 
   __syncthreads();
 }
 
-__device__ __forceinline__ void syn2_any(int b, const Syn2& s, int l, int r0, int c0, float* sh, float acc[4]) {
+__device__ __forceinline__ void syn2_stage_any(int b, const Syn2& s, int l, int r0, int c0, float* tc) {
   switch (b) {
-    case 0: syn2_tile<2>(s, l, r0, c0, sh, acc); break;
-    case 1: syn2_tile<4>(s, l, r0, c0, sh, acc); break;
-    case 2: syn2_tile<6>(s, l, r0, c0, sh, acc); break;
-    case 3: syn2_tile<8>(s, l, r0, c0, sh, acc); break;
-    case 4: syn2_tile<10>(s, l, r0, c0, sh, acc); break;
-    case 5: syn2_tile<12>(s, l, r0, c0, sh, acc); break;
-    case 6: syn2_tile<14>(s, l, r0, c0, sh, acc); break;
-    default: syn2_tile<16>(s, l, r0, c0, sh, acc); break;
+    case 0: syn2_stage<2>(s, l, r0, c0, tc); break;
+    case 1: syn2_stage<4>(s, l, r0, c0, tc); break;
+    case 2: syn2_stage<6>(s, l, r0, c0, tc); break;
+    case 3: syn2_stage<8>(s, l, r0, c0, tc); break;
+    case 4: syn2_stage<10>(s, l, r0, c0, tc); break;
+    case 5: syn2_stage<12>(s, l, r0, c0, tc); break;
+    case 6: syn2_stage<14>(s, l, r0, c0, tc); break;
+    default: syn2_stage<16>(s, l, r0, c0, tc); break;
+  }
+}
+
+__device__ __forceinline__ void syn2_compute_any(int b, const float* tc, float* lx, float* hx, float lls,
+                                                 float acc[4]) {
+  switch (b) {
+    case 0: syn2_compute<2>(tc, lx, hx, lls, acc); break;
+    case 1: syn2_compute<4>(tc, lx, hx, lls, acc); break;
+    case 2: syn2_compute<6>(tc, lx, hx, lls, acc); break;
+    case 3: syn2_compute<8>(tc, lx, hx, lls, acc); break;
+    case 4: syn2_compute<10>(tc, lx, hx, lls, acc); break;
+    case 5: syn2_compute<12>(tc, lx, hx, lls, acc); break;
+    case 6: syn2_compute<14>(tc, lx, hx, lls, acc); break;
+    default: syn2_compute<16>(tc, lx, hx, lls, acc); break;
   }
 }
 
 template <int F>
 __global__ void __launch_bounds__(256) k_syn2(Syn2 s, float* __restrict__ out) {
-  __shared__ float sh[4 * kKn2 * (kKn2 + 1) + 2 * kT2 * (kKn2 + 1)];
+  __shared__ float sh[4 * kTS2 + 2 * kT2 * (kKn2 + 1)];
   const int l = blockIdx.z;
   const int r0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  syn2_tile<F>(s, l, r0, c0, sh, acc);
+  syn2_stage<F>(s, l, r0, c0, sh);
+  cp_async_wait<0>();
+  __syncthreads();
+  syn2_compute<F>(sh, sh + 4 * kTS2, sh + 4 * kTS2 + kT2 * (kKn2 + 1), s.ll ? 1.f : 1.f / 3.f, acc);
   const int il = threadIdx.x >> 3, jc0 = 4 * (threadIdx.x & 7);
   const int r = r0 + il;
   if (r >= s.m1) return;
@@ -275,13 +320,28 @@ struct SynFin2 {
   float kappa;
 };
 
+// Level 1 of all bases: the tiles of basis b + 1 are staged (cp.async) while basis b
+// is computed.
 __global__ void __launch_bounds__(256) k_synfin(SynFin2 s, float* __restrict__ A) {
-  __shared__ float sh[4 * kKn2 * (kKn2 + 1) + 2 * kT2 * (kKn2 + 1)];
+  __shared__ float sh[2 * 4 * kTS2 + 2 * kT2 * (kKn2 + 1)];
+  float* tcb[2] = {sh, sh + 4 * kTS2};
+  float* lx = sh + 8 * kTS2;
+  float* hx = lx + kT2 * (kKn2 + 1);
   const int l = blockIdx.z;
   const int r0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  syn2_stage_any(0, s.lv[0], l, r0, c0, tcb[0]);
 #pragma unroll 1
-  for (int b = 0; b < 8; ++b) syn2_any(b, s.lv[b], l, r0, c0, sh, acc);
+  for (int b = 0; b < 8; ++b) {
+    if (b + 1 < 8) {
+      syn2_stage_any(b + 1, s.lv[b + 1], l, r0, c0, tcb[(b + 1) & 1]);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    syn2_compute_any(b, tcb[b & 1], lx, hx, 1.f, acc);
+  }
   const int il = threadIdx.x >> 3, jc0 = 4 * (threadIdx.x & 7);
   const int r = r0 + il;
   if (r >= s.n1) return;
