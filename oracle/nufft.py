@@ -136,6 +136,42 @@ def adjoint(v: np.ndarray, uv: np.ndarray, n1: int, n2: int) -> np.ndarray:
     return s * full[np.ix_(rows, cols)]
 
 
+def measure_sampled(x: np.ndarray, uv: np.ndarray) -> np.ndarray:
+    """Phi x (Eq. 1) at a few visibilities without an FFT: the 7 x 7 grid values each
+    visibility reads are DFT sums of the scaled image, taken as E_r (s x) E_c^T with
+    E[k][p] = exp(-2 pi i k p / K) over the tap rows and columns, then weighted by the
+    Kaiser-Bessel taps.  For checks of large images at sampled outputs."""
+    n1, n2 = x.shape
+    K1, K2 = 2 * n1, 2 * n2
+    uv = np.asarray(uv, dtype=np.float64)
+    kr, wr = taps(uv[:, 1] * K1 / (2.0 * np.pi))          # [S][7]
+    kc, wc = taps(uv[:, 0] * K2 / (2.0 * np.pi))
+    sx = np.outer(scaling(n1, K1), scaling(n2, K2)) * x
+    er = np.exp(-2j * np.pi * np.outer(kr.ravel(), pixel_coords(n1)) / K1)   # [7S][n1]
+    ec = np.exp(-2j * np.pi * np.outer(kc.ravel(), pixel_coords(n2)) / K2)   # [7S][n2]
+    rows = (er @ sx).reshape(len(uv), J, n2)                                  # [S][7][n2]
+    g = np.einsum("mic,mjc->mij", rows, ec.reshape(len(uv), J, n2))
+    return np.einsum("mi,mj,mij->m", wr, wc, g)
+
+
+def adjoint_real_sampled(v: np.ndarray, uv: np.ndarray, n1: int, n2: int, pix) -> np.ndarray:
+    """Re Phi^dagger v at a few pixels (r, c) by direct summation over visibilities and
+    taps: s_r s_c Re sum_m v_m (sum_i w_i e^{2 pi i k_i p_r / K1}) (sum_j w_j e^{2 pi i k_j p_c / K2})."""
+    K1, K2 = 2 * n1, 2 * n2
+    uv = np.asarray(uv, dtype=np.float64)
+    v = np.asarray(v, dtype=np.complex128)
+    kr, wr = taps(uv[:, 1] * K1 / (2.0 * np.pi))
+    kc, wc = taps(uv[:, 0] * K2 / (2.0 * np.pi))
+    sr, sc = scaling(n1, K1), scaling(n2, K2)
+    pr, pc = pixel_coords(n1), pixel_coords(n2)
+    out = np.empty(len(pix))
+    for i, (r, c) in enumerate(pix):
+        ar = (wr * np.exp(2j * np.pi * kr * pr[r] / K1)).sum(axis=1)
+        ac = (wc * np.exp(2j * np.pi * kc * pc[c] / K2)).sum(axis=1)
+        out[i] = sr[r] * sc[c] * np.real(np.sum(v * ar * ac))
+    return out
+
+
 def measure_cube(x: np.ndarray, uv: np.ndarray, M_l) -> np.ndarray:
     """Phi applied channel by channel; uv and the result are channel-major."""
     out, off = [], 0
@@ -155,5 +191,6 @@ def adjoint_cube_real(v: np.ndarray, uv: np.ndarray, M_l, n1: int, n2: int) -> n
 
 
 __all__ = ["J", "BETA", "kb_kernel", "kb_kernel_ft", "pixel_coords", "scaling", "direct_dft",
-           "zpad_fft", "taps", "degrid", "grid_adjoint", "measure", "adjoint",
+           "zpad_fft", "taps", "degrid", "grid_adjoint", "measure", "adjoint", "measure_sampled",
+           "adjoint_real_sampled",
            "measure_cube", "adjoint_cube_real"]

@@ -158,9 +158,25 @@ __global__ void __launch_bounds__(ColCfg<N>::NT) k_colA_adj(const float2* __rest
   }
 }
 
+#include "fft_reg.cuh"
+
 // ------------------------------------------------------------- dispatch
+template <int N, bool INV>
+static void rowr_n(const Cube& cb, float2* grid, const float2* tw, int Kmax, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_rowr<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegRow<N>::SMEM); attr = true; }
+  dim3 grd(cb.K1, cb.L);
+  k_rowr<N, INV><<<grd, RegRow<N>::NT, RegRow<N>::SMEM, st>>>(grid, cb.K1, cb.n2, tw, Kmax / N);
+  note_launches(1);
+}
+
 template <int N>
 static void row2_n(const Cube& cb, float2* grid, int inv, const float2* tw, int Kmax, cudaStream_t st) {
+  if constexpr (N >= 2048) {
+    if (inv) rowr_n<N, true>(cb, grid, tw, Kmax, st);
+    else rowr_n<N, false>(cb, grid, tw, Kmax, st);
+    return;
+  }
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_row2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
   constexpr int S = Row2Cfg<N>::S;

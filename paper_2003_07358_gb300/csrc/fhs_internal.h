@@ -91,6 +91,8 @@ struct Scratch {
   float* blk_scale = nullptr;                           // [L*B]
   double* blk_out = nullptr;                            // [2][L*B]
   float* ll1 = nullptr;                                 // synthesised LL1 band of each basis (fused SARA)
+  double* stat = nullptr;                               // per cube: primal partials, then block norms
+  size_t stat_stride = 0;
   int64_t ll1_off[8] = {0};                             // per-basis offsets into ll1
 };
 
@@ -105,6 +107,12 @@ struct fhs_ctx {
   std::string err;
   bool broken = false;
   int path = FHS_PATH_FAST;        // FHS_PATH_FAST or FHS_PATH_PLAIN
+  // CUDA graph of one PDFB iteration of every cube, replayed on gstream
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<const void*> graph_key;
+  uint64_t graph_kernels = 0;
 };
 
 namespace fhs {

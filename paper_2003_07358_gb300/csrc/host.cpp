@@ -486,7 +486,7 @@ void alloc_scratch(fhs_ctx* ctx) {
     red = std::max(red, L * 64 * 2);
     int nch = (cb.max_facet_pix + 1023) / 1024;
     gram = std::max(gram, (size_t)cb.facets.size() * nch * L * L);
-    nm = std::max(nm, (size_t)cb.facets.size() * L * L);
+    nm = std::max(nm, (size_t)cb.facets.size() * L * ((L + 3) & ~3));   // M_q^T rows padded to 16 B
     lb = std::max(lb, L * cb.B);
   }
   size_t ll1 = 0;
@@ -509,11 +509,13 @@ void alloc_scratch(fhs_ctx* ctx) {
   s.nucM = dalloc<float>(nm); s.nucM_elems = nm;
   s.blk_scale = dalloc<float>(lb);
   s.blk_out = dalloc<double>(2 * lb + 2 * kMaxL);
+  s.stat_stride = 2 * 1216 + 2 * lb;
+  s.stat = dalloc<double>(s.stat_stride * ctx->cubes.size());
 }
 
 void free_scratch(Scratch& s) {
   void* ps[] = {s.grid, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.img2, s.vis, s.red, s.gram, s.nucM, s.blk_scale,
-                s.blk_out, s.ll1};
+                s.blk_out, s.ll1, s.stat};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (s.red_host) cudaFreeHost(s.red_host);
@@ -564,6 +566,34 @@ void adjoint_into(fhs_ctx* ctx, const Cube& cb, const float2* vals, const float*
   check_launch("adjoint");
 }
 
+// One iteration of Algorithm 2 on every cube, on ctx->stream; the primal partial
+// sums and the block norms of cube c land in its statistics region.
+void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
+  cudaStream_t st = ctx->stream;
+  const int nc = (int)ctx->cubes.size();
+  for (int c = 0; c < nc; ++c) {
+    const Cube& cb = ctx->cubes[c];
+    const fhs_iterate& a = it[c];
+    float* A = ctx->s.img;
+    const size_t nimg = (size_t)cb.L * cb.n1 * cb.n2;
+    double* stat = ctx->s.stat + ctx->s.stat_stride * c;
+    const int pp = primal_parts(cb);
+    FHS_CUDA(cudaMemsetAsync(A, 0, nimg * sizeof(float), st));
+    launch_nuclear(ctx, cb, a.Xcheck, a.state.P, a.state.theta_bar, A, false, nullptr, st);
+    check_launch("nuclear dual");
+    sara_dual(ctx, cb, a.Xcheck, a.state.W, a.state.theta, A);
+    // data fidelity: x_hat = F Z x, degrid + l2-ball duals, grid, adjoint
+    launch_fft_forward(ctx, cb, a.X, ctx->s.grid, st);
+    int np = degrid_parts(cb);
+    launch_degrid_pdfb(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
+                       (float2*)a.state.u_prev, ctx->s.red, np, st);
+    launch_block_finalize(cb, ctx->s.red, np, ctx->s.blk_scale, stat + 2 * pp, st);
+    adjoint_into(ctx, cb, ctx->s.vis, ctx->s.blk_scale, (float2*)a.state.v, A, cb.d_eta, true);
+    launch_primal(cb, a.X, a.Xcheck, A, stat, pp, st);
+    check_launch("primal");
+  }
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -601,6 +631,9 @@ fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, 
     ctx->d_tw = dalloc<float2>(kmax);
     upload(ctx->d_tw, tw.data(), tw.size(), ctx->stream);
     alloc_scratch(ctx);
+    FHS_CUDA(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+    FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+    FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
     FHS_CUDA(cudaStreamSynchronize(ctx->stream));
   } catch (const Fail& e) {
     g_create_err = e.msg;
@@ -617,6 +650,11 @@ fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, 
 fhs_status fhs_destroy(fhs_ctx* ctx) {
   if (!ctx) return FHS_ERR_INVALID_ARG;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   for (Cube& cb : ctx->cubes) free_cube(cb);
   free_scratch(ctx->s);
   if (ctx->d_tw) cudaFree(ctx->d_tw);
@@ -856,58 +894,75 @@ fhs_status fhs_set_path(fhs_ctx* ctx, int32_t path) {
 fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fhs_iter_stats* stats) {
   return guarded(ctx, [&] {
     FHS_REQUIRE(it && n_iter >= 0, FHS_ERR_INVALID_ARG, "bad arguments");
-    cudaStream_t st = ctx->stream;
     const int nc = (int)ctx->cubes.size();
+    std::vector<const void*> key;
+    key.push_back((const void*)(intptr_t)ctx->path);
     for (int c = 0; c < nc; ++c) {
       const fhs_iterate& a = it[c];
       FHS_REQUIRE(a.X && a.Xcheck && a.y && a.state.W && a.state.theta && a.state.P && a.state.theta_bar &&
                       a.state.v && a.state.u_prev,
                   FHS_ERR_INVALID_ARG, "NULL array in fhs_iterate");
+      const void* ps[] = {a.X, a.Xcheck, a.y, a.state.W, a.state.theta, a.state.P, a.state.theta_bar, a.state.v,
+                          a.state.u_prev};
+      key.insert(key.end(), ps, ps + 9);
     }
-    std::vector<double> primal_host, blk_host;
-    for (int p = 0; p < n_iter; ++p) {
-      const bool last = (p == n_iter - 1);
-      for (int c = 0; c < nc; ++c) {
-        const Cube& cb = ctx->cubes[c];
-        const fhs_iterate& a = it[c];
-        float* A = ctx->s.img;
-        const size_t nimg = (size_t)cb.L * cb.n1 * cb.n2;
-        FHS_CUDA(cudaMemsetAsync(A, 0, nimg * sizeof(float), st));
-        launch_nuclear(ctx, cb, a.Xcheck, a.state.P, a.state.theta_bar, A, false, nullptr, st);
-        check_launch("nuclear dual");
-        sara_dual(ctx, cb, a.Xcheck, a.state.W, a.state.theta, A);
-        // data fidelity: x_hat = F Z x, degrid + l2-ball duals, grid, adjoint
-        launch_fft_forward(ctx, cb, a.X, ctx->s.grid, st);
-        int np = degrid_parts(cb);
-        launch_degrid_pdfb(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
-                           (float2*)a.state.u_prev, ctx->s.red, np, st);
-        launch_block_finalize(cb, ctx->s.red, np, ctx->s.blk_scale, ctx->s.blk_out, st);
-        adjoint_into(ctx, cb, ctx->s.vis, ctx->s.blk_scale, (float2*)a.state.v, A, cb.d_eta, true);
-        // primal update
-        int pp = primal_parts(cb);
-        launch_primal(cb, a.X, a.Xcheck, A, ctx->s.red, pp, st);
-        check_launch("primal");
-        if (last && stats) {
-          primal_host.resize(2 * pp);
-          blk_host.resize(2 * cb.L * cb.B);
-          FHS_CUDA(cudaMemcpyAsync(primal_host.data(), ctx->s.red, 2 * pp * sizeof(double), cudaMemcpyDeviceToHost, st));
-          FHS_CUDA(cudaMemcpyAsync(blk_host.data(), ctx->s.blk_out, 2 * cb.L * cb.B * sizeof(double),
-                                   cudaMemcpyDeviceToHost, st));
-          FHS_CUDA(cudaStreamSynchronize(st));
-          double dx2 = 0.0, x2 = 0.0;
-          for (int k = 0; k < pp; ++k) { dx2 += primal_host[2 * k]; x2 += primal_host[2 * k + 1]; }
-          double r2 = 0.0, e2 = 0.0;
-          for (int k = 0; k < cb.L * cb.B; ++k) {
-            r2 += blk_host[cb.L * cb.B + k] * blk_host[cb.L * cb.B + k];
-            e2 += cb.eps[k] * cb.eps[k];
-          }
-          FHS_REQUIRE(std::isfinite(dx2) && std::isfinite(x2) && std::isfinite(r2), FHS_ERR_NONFINITE,
-                      "non-finite iteration statistics");
-          stats[c].xi = x2 > 0 ? sqrt(dx2 / x2) : INFINITY;
-          stats[c].res_norm = sqrt(r2);
-          stats[c].eps_norm = sqrt(e2);
-        }
+    if (n_iter == 0) return;
+    // (re)capture one iteration of every cube into a CUDA graph when the arrays or the path change
+    if (!ctx->graph_exec || key != ctx->graph_key) {
+      if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+      ensure_coef(ctx);   // no allocation may happen inside the capture
+      cudaStream_t user = ctx->stream;
+      uint64_t before = g_launches.load();
+      FHS_CUDA(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+      ctx->stream = ctx->gstream;
+      try {
+        pdfb_iteration(ctx, it);
+      } catch (...) {
+        ctx->stream = user;
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(ctx->gstream, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
       }
+      ctx->stream = user;
+      cudaGraph_t g = nullptr;
+      FHS_CUDA(cudaStreamEndCapture(ctx->gstream, &g));
+      cudaError_t e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      FHS_CUDA(e);
+      ctx->graph_kernels = g_launches.load() - before;
+      g_launches.fetch_sub(ctx->graph_kernels);          // captured, not launched
+      ctx->graph_key = key;
+    }
+    FHS_CUDA(cudaEventRecord(ctx->ev_in, ctx->stream));
+    FHS_CUDA(cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0));
+    for (int p = 0; p < n_iter; ++p) {
+      FHS_CUDA(cudaGraphLaunch(ctx->graph_exec, ctx->gstream));
+      note_launches((int)ctx->graph_kernels);
+    }
+    FHS_CUDA(cudaEventRecord(ctx->ev_out, ctx->gstream));
+    FHS_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0));
+    if (!stats) return;
+    std::vector<double> h(ctx->s.stat_stride * nc);
+    FHS_CUDA(cudaMemcpyAsync(h.data(), ctx->s.stat, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    FHS_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < nc; ++c) {
+      const Cube& cb = ctx->cubes[c];
+      const double* st = h.data() + ctx->s.stat_stride * c;
+      const int pp = primal_parts(cb);
+      const double* blk = st + 2 * pp;
+      double dx2 = 0.0, x2 = 0.0;
+      for (int k = 0; k < pp; ++k) { dx2 += st[2 * k]; x2 += st[2 * k + 1]; }
+      double r2 = 0.0, e2 = 0.0;
+      for (int k = 0; k < cb.L * cb.B; ++k) {
+        r2 += blk[cb.L * cb.B + k] * blk[cb.L * cb.B + k];
+        e2 += cb.eps[k] * cb.eps[k];
+      }
+      FHS_REQUIRE(std::isfinite(dx2) && std::isfinite(x2) && std::isfinite(r2), FHS_ERR_NONFINITE,
+                  "non-finite iteration statistics");
+      stats[c].xi = x2 > 0 ? sqrt(dx2 / x2) : INFINITY;
+      stats[c].res_norm = sqrt(r2);
+      stats[c].eps_norm = sqrt(e2);
     }
   });
 }

@@ -271,20 +271,25 @@ __global__ void __launch_bounds__(32) k_eig(const double* __restrict__ part, int
     lam[j] = (s > alpha) ? alpha / s : 1.0;
   }
   __syncwarp();
-  for (int idx = lane; idx < L * L; idx += 32) {
-    int a = idx / L, b = idx % L;
+  // M_q^T, rows padded to Lp = L rounded up to 4 (zeros), so that a row is read as float4
+  const int Lp = (L + 3) & ~3;
+  for (int idx = lane; idx < L * Lp; idx += 32) {
+    int b = idx / Lp, a = idx % Lp;
     double m = 0.0;
-    for (int j = 0; j < L; ++j) m += V[a * Ls + j] * lam[j] * V[b * Ls + j];
-    Mout[(size_t)q * L * L + idx] = (float)m;
+    if (a < L)
+      for (int j = 0; j < L; ++j) m += V[a * Ls + j] * lam[j] * V[b * Ls + j];
+    Mout[(size_t)q * L * Lp + idx] = (float)m;
   }
 }
 
 // Pixel-driven update: each thread owns one pixel; for every facet covering it,
-// z = P_q + D_q x, P_q <- z M_q, A += zeta D_q P_q.
+// z = P_q + D_q x, P_q <- z M_q, A += zeta D_q P_q.  Row b of M_q^T is read as
+// float4 (one load per four FMAs, the same address across the warp), and A is
+// updated per facet so that only z lives in registers.
 template <int LMAX>
 __global__ void __launch_bounds__(256) k_apply(const float* __restrict__ xc, float* __restrict__ P,
                                                const NucFacet* __restrict__ facets, const float* __restrict__ win,
-                                               const float* __restrict__ M, int n1, int n2, int L, int Qy, int Qx,
+                                               const float* __restrict__ Mt, int n1, int n2, int L, int Qy, int Qx,
                                                const int* __restrict__ ty_of, const int* __restrict__ tx_of,
                                                float zeta, float* __restrict__ A) {
   const int c = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -292,12 +297,7 @@ __global__ void __launch_bounds__(256) k_apply(const float* __restrict__ xc, flo
   if (r >= n1 || c >= n2) return;
   const size_t N = (size_t)n1 * n2;
   const size_t pix = (size_t)r * n2 + c;
-  float x[LMAX], acc[LMAX];
-#pragma unroll
-  for (int l = 0; l < LMAX; ++l) {
-    x[l] = (l < L) ? xc[l * N + pix] : 0.f;
-    acc[l] = 0.f;
-  }
+  const int Lp = (L + 3) & ~3;
   const int ty = ty_of[r], tx = tx_of[c];
   for (int dy = 0; dy < 2; ++dy) {
     int qy = ty + dy;
@@ -314,24 +314,28 @@ __global__ void __launch_bounds__(256) k_apply(const float* __restrict__ xc, flo
       float* Pq = P + f.p_off;
       float z[LMAX];
 #pragma unroll
-      for (int l = 0; l < LMAX; ++l) z[l] = (l < L) ? fmaf(d, x[l], Pq[(size_t)l * Nq + p]) : 0.f;
-      const float* Mq = M + (size_t)(qy * Qx + qx) * L * L;
+      for (int l = 0; l < LMAX; ++l) z[l] = (l < L) ? fmaf(d, xc[l * N + pix], Pq[(size_t)l * Nq + p]) : 0.f;
+      const float4* Mq = reinterpret_cast<const float4*>(Mt + (size_t)(qy * Qx + qx) * L * Lp);
+      const float zd = zeta * d;
+#pragma unroll 1
+      for (int b = 0; b < L; ++b) {
+        const float4* row = Mq + (size_t)b * (Lp / 4);
+        float s = 0.f;
 #pragma unroll
-      for (int b = 0; b < LMAX; ++b) {
-        if (b < L) {
-          float s = 0.f;
-#pragma unroll
-          for (int a = 0; a < LMAX; ++a)
-            if (a < L) s = fmaf(z[a], __ldg(&Mq[a * L + b]), s);
-          Pq[(size_t)b * Nq + p] = s;
-          acc[b] = fmaf(zeta * d, s, acc[b]);
+        for (int a4 = 0; a4 < LMAX / 4; ++a4) {
+          if (4 * a4 < L) {
+            const float4 m = __ldg(row + a4);
+            s = fmaf(z[4 * a4], m.x, s);
+            s = fmaf(z[4 * a4 + 1], m.y, s);
+            s = fmaf(z[4 * a4 + 2], m.z, s);
+            s = fmaf(z[4 * a4 + 3], m.w, s);
+          }
         }
+        Pq[(size_t)b * Nq + p] = s;
+        A[b * N + pix] = fmaf(zd, s, A[b * N + pix]);
       }
     }
   }
-#pragma unroll
-  for (int l = 0; l < LMAX; ++l)
-    if (l < L) A[l * N + pix] += acc[l];
 }
 
 static int nchunk_max(const Cube& cb) { return (cb.max_facet_pix + kGramChunk - 1) / kGramChunk; }

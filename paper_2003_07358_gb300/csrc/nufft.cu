@@ -632,31 +632,90 @@ __global__ void k_l2ball_scale(const float2* __restrict__ d, const float* __rest
 // each visibility lands in exactly one (tile, pass).
 // Class order within a tile: 0 interior, 1 crosses down only, 2 crosses down
 // and right, 3 crosses right only.
-__global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
+// Accumulation is in fixed point with integer shared-memory atomics (much faster
+// than floating-point ones, and order-independent, so the result is bitwise
+// deterministic).  A first sweep over the CTA's visibilities gives
+// bound = max(sum |Re val|, sum |Im val|) >= |any cell sum| (Kaiser-Bessel weights
+// are <= 1); values are scaled by S = 2^e with bound * S < 2^(bits - 3) and rounded to
+// integers, so nothing can overflow, and the cell is read back as acc / S.
+template <typename Acc> struct FixedAcc;
+template <> struct FixedAcc<int> {
+  static constexpr int kBits = 32;
+  __device__ static void add(int* p, float v) { atomicAdd(p, __float2int_rn(v)); }
+};
+template <> struct FixedAcc<long long> {
+  static constexpr int kBits = 64;
+  __device__ static void add(long long* p, float v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__float2ll_rn(v));
+  }
+};
+
+// Source range [beg, end) of pass (dr, dc) for destination tile (tr, tc).
+__device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, int tr, int tc, int ntr, int ntc,
+                                                int& sr, int& sc, int& beg, int& end) {
+  const int dr = pass >> 1, dc = pass & 1;
+  sr = (tr - dr + ntr) % ntr;
+  sc = (tc - dc + ntc) % ntc;
+  const int sidx = (sr * ntc + sc) * 4;
+  if (pass == 0) { beg = toff[sidx]; end = toff[sidx + 4]; }
+  else if (pass == 1) { beg = toff[sidx + 2]; end = toff[sidx + 4]; }   // crosses right: classes 2, 3
+  else if (pass == 2) { beg = toff[sidx + 1]; end = toff[sidx + 3]; }   // crosses down: classes 1, 2
+  else { beg = toff[sidx + 2]; end = toff[sidx + 3]; }                  // crosses both: class 2
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
                                               float2* __restrict__ v_write, const float2* __restrict__ uv,
                                               const uint8_t* __restrict__ blk, const int32_t* __restrict__ tile_off,
                                               const int64_t* __restrict__ vis_off, float2* __restrict__ grid,
                                               VisGeom vg, int T, int ntr, int ntc, int B) {
-  extern __shared__ float sacc[];
+  extern __shared__ __align__(16) unsigned char sraw[];
+  __shared__ float sbound[2][8];
+  Acc* are = reinterpret_cast<Acc*>(sraw);
   const int TP = T + 1;                  // padded row stride: banks (row + col) mod 32
-  float* are = sacc;
-  float* aim = sacc + T * TP;
+  Acc* aim = are + T * TP;
   const int l = blockIdx.y;
   const int tau = blockIdx.x;
   const int tr = tau / ntc, tc = tau % ntc;
-  for (int k = threadIdx.x; k < 2 * T * TP; k += blockDim.x) sacc[k] = 0.f;
-  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * T * TP; k += blockDim.x) are[k] = 0;
   const int64_t vbase = vis_off[l];
   const int32_t* toff = tile_off + (size_t)l * (ntr * ntc * 4 + 1);
+  // sweep 1: bound on any cell of this tile
+  float bx = 0.f, by = 0.f;
+  for (int pass = 0; pass < 4; ++pass) {
+    int sr, sc, beg, end;
+    grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
+    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
+      const int64_t i = vbase + k;
+      float2 val = vals[i];
+      const float s = blk_scale ? blk_scale[l * B + blk[i]] : 1.f;
+      bx += fabsf(val.x * s);
+      by += fabsf(val.y * s);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bx += __shfl_xor_sync(0xffffffffu, bx, o);
+    by += __shfl_xor_sync(0xffffffffu, by, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sbound[0][threadIdx.x >> 5] = bx;
+    sbound[1][threadIdx.x >> 5] = by;
+  }
+  __syncthreads();
+  float bound = 0.f;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) bound = fmaxf(bound, fmaxf(sbound[0][w], sbound[1][w]));
+  // S = 2^e, bound * S < 2^(bits - 3); the 1.01 covers the rounding of the FP32 sum
+  // (ex from the exponent field: bound * 1.01 < 2^ex; zero or subnormal bound gives ex = -126)
+  const int ex = (int)((__float_as_uint(bound * 1.01f) >> 23) & 0xffu) - 126;
+  const int e = min(FixedAcc<Acc>::kBits - 3 - ex, 120);
+  const float S = __uint_as_float((unsigned)(e + 127) << 23), invS = __uint_as_float((unsigned)(127 - e) << 23);
+  // sweep 2: taps
   for (int pass = 0; pass < 4; ++pass) {
     const int dr = pass >> 1, dc = pass & 1;
-    const int sr = (tr - dr + ntr) % ntr, sc = (tc - dc + ntc) % ntc;
-    const int sidx = (sr * ntc + sc) * 4;
-    int beg, end;
-    if (pass == 0) { beg = toff[sidx]; end = toff[sidx + 4]; }
-    else if (pass == 1) { beg = toff[sidx + 2]; end = toff[sidx + 4]; }   // crosses right: classes 2, 3
-    else if (pass == 2) { beg = toff[sidx + 1]; end = toff[sidx + 3]; }   // crosses down: classes 1, 2
-    else { beg = toff[sidx + 2]; end = toff[sidx + 3]; }                  // crosses both: class 2
+    int sr, sc, beg, end;
+    grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
     for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
       const int64_t i = vbase + k;
       float2 w = uv[i];
@@ -676,6 +735,7 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
       const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
       const int a0 = max(0, -lr), a1 = min(kTaps, T - lr);
       const int b0 = max(0, -lc), b1 = min(kTaps, T - lc);
+      const float vx = val.x * S, vy = val.y * S;
       // rolled, warp-uniform row loop (the row weight is evaluated in the loop) keeps
       // the register count low; the 7 column weights stay in registers
 #pragma unroll 1
@@ -683,12 +743,12 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
         if (a < a0 || a >= a1) continue;
         const float wa = kb_tap(a, xr);
         const int rowoff = (lr + a) * TP + lc;
-        const float va = wa * val.x, vb = wa * val.y;
+        const float va = wa * vx, vb = wa * vy;
 #pragma unroll
         for (int b = 0; b < kTaps; ++b) {
           if (b < b0 || b >= b1) continue;
-          atomicAdd(&are[rowoff + b], wc[b] * va);
-          atomicAdd(&aim[rowoff + b], wc[b] * vb);
+          FixedAcc<Acc>::add(&are[rowoff + b], wc[b] * va);
+          FixedAcc<Acc>::add(&aim[rowoff + b], wc[b] * vb);
         }
       }
     }
@@ -698,11 +758,14 @@ __global__ void __launch_bounds__(256) k_grid(const float2* __restrict__ vals, c
   for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
     int rr = k / T, cc = k % T;
     int row = phys_row2(tr * T + rr, vg);
-    gl[(size_t)row * vg.K2 + tc * T + cc] = make_float2(are[rr * TP + cc], aim[rr * TP + cc]);
+    gl[(size_t)row * vg.K2 + tc * T + cc] =
+        make_float2((float)are[rr * TP + cc] * invS, (float)aim[rr * TP + cc] * invS);
   }
 }
 
 // ------------------------------------------------------------- launchers
+using kGridAcc = long long;            // fixed-point accumulator of the gridder
+
 static VisGeom vis_geom(const Cube& cb) {
   VisGeom vg;
   vg.K1 = cb.K1; vg.K2 = cb.K2; vg.N1c = cb.N1c; vg.N2c = cb.N2c;
@@ -750,12 +813,13 @@ void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, fl
 
 void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write, float2* grid,
                  cudaStream_t st) {
+  using Acc = kGridAcc;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024); attr = true; }
+  if (!attr) { cudaFuncSetAttribute(k_grid<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
-  size_t sm = 2 * (size_t)cb.tile * (cb.tile + 1) * sizeof(float);
-  k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
-                               vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
+  size_t sm = 2 * (size_t)cb.tile * (cb.tile + 1) * sizeof(Acc);
+  k_grid<Acc><<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
+                                    vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
 }
 

@@ -29,10 +29,22 @@ __device__ __forceinline__ void cta_sum2(double a, double b, double* out) {
   }
 }
 
+// Compensated (Kahan) FP32 running sum; the FP64 pipe of the SM is kept for the
+// final per-thread totals only.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
 __global__ void __launch_bounds__(256) k_primal(float4* __restrict__ X, float4* __restrict__ Xc,
                                                 const float4* __restrict__ A, float tau, int64_t n4,
                                                 double* __restrict__ partials) {
-  double dx2 = 0.0, x2 = 0.0;
+  KahanF dx2, x2;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
     float4 x = X[i], a = A[i];
     float4 xn;
@@ -47,11 +59,11 @@ __global__ void __launch_bounds__(256) k_primal(float4* __restrict__ X, float4* 
     xc.w = 2.f * xn.w - x.w;
     X[i] = xn;
     Xc[i] = xc;
-    double d0 = (double)xn.x - x.x, d1 = (double)xn.y - x.y, d2 = (double)xn.z - x.z, d3 = (double)xn.w - x.w;
-    dx2 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
-    x2 += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+    const float d0 = xn.x - x.x, d1 = xn.y - x.y, d2 = xn.z - x.z, d3 = xn.w - x.w;
+    dx2.add(fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, d3 * d3))));
+    x2.add(fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w))));
   }
-  cta_sum2<256>(dx2, x2, partials + 2 * blockIdx.x);
+  cta_sum2<256>((double)dx2.s - (double)dx2.c, (double)x2.s - (double)x2.c, partials + 2 * blockIdx.x);
 }
 
 int primal_parts(const Cube&) { return kPrimalCTAs; }

@@ -7,7 +7,7 @@
 //                 register blocking (each thread produces 4 outputs from one
 //                 window of F + 6 loaded values); writes the LL band for the
 //                 next level and the detail bands (/3) to the coefficient buffer.
-//   k_prox2<L>  : the l2,1 dual over every coefficient of the sub-cube in one
+//   k_prox2     : the l2,1 dual over every coefficient of the sub-cube in one
 //                 streaming pass (Dirac block read straight from x):
 //                 W <- z min(1, alpha_i / ||z_i||), z = W + Psi^dagger x
 //                 (weights mode: theta_i = mu / (||Psi^dagger x||_i + mu)).
@@ -25,15 +25,18 @@ constexpr int kT2 = 32;                              // tile side (coefficients 
 constexpr int kIn2 = 2 * kT2 + kMaxFilt - 2;         // 78: input rows/cols of an analysis tile
 constexpr int kKn2 = kT2 / 2 + kMaxFilt / 2;         // 24: coefficient rows/cols of a synthesis tile
 
+// Filter taps of basis F/2 - 1.  With compile-time indices the FMAs take them as
+// constant-bank operands, so they occupy no registers.
 template <int F>
 struct FTaps {
-  float h[F], g[F];
+  struct Row {
+    const float* p;
+    __device__ __forceinline__ float operator[](int t) const { return p[t]; }
+  };
+  Row h, g;
   __device__ __forceinline__ void load() {
-#pragma unroll
-    for (int t = 0; t < F; ++t) {
-      h[t] = c_filt.h[F / 2 - 1][t];
-      g[t] = c_filt.g[F / 2 - 1][t];
-    }
+    h.p = c_filt.h[F / 2 - 1];
+    g.p = c_filt.g[F / 2 - 1];
   }
 };
 
@@ -115,52 +118,33 @@ __global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, floa
 }
 
 // ---------------------------------------------------------- l2,1 dual
-// Each warp takes 64 consecutive coefficients (two per lane, 32 apart), so every
-// channel plane is read in 256-byte runs: better DRAM page locality than one
-// coefficient per lane across 2L planes.
-template <int LMAX>
-__global__ void __launch_bounds__(256) k_prox2(float* __restrict__ W, const float* __restrict__ coef,
+// One coefficient per thread; z of every channel is parked in shared memory
+// (L x 256 floats) instead of registers, so the kernel runs at full occupancy
+// with 2L independent loads in flight per thread.
+__global__ void __launch_bounds__(256, 4) k_prox2(float* __restrict__ W, const float* __restrict__ coef,
                                                const float* __restrict__ x, const float* __restrict__ theta,
                                                float* __restrict__ theta_out, int64_t I, int64_t dirac_off, int64_t N,
                                                int L, float alpha_scale, float mu, int weights) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 64; base < I; base += nwarps * 64) {
-    int64_t ii[2] = {base + lane, base + 32 + lane};
-    float z[2][LMAX];
-    float n2[2] = {0.f, 0.f};
-#pragma unroll
-    for (int l = 0; l < LMAX; ++l) {
-      if (l < L) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int64_t i = ii[k];
-          float v = 0.f;
-          if (i < I) {
-            float c = i >= dirac_off ? x[(size_t)l * N + (i - dirac_off)] * (1.f / 3.f) : coef[(size_t)l * I + i];
-            v = weights ? c : W[(size_t)l * I + i] + c;
-          }
-          z[k][l] = v;
-          n2[k] = fmaf(v, v, n2[k]);
-        }
-      }
+  extern __shared__ float zs[];                         // [L][256]
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool dirac = i >= dirac_off;
+    float n2 = 0.f;
+#pragma unroll 16
+    for (int l = 0; l < L; ++l) {
+      float c = dirac ? x[(size_t)l * N + (i - dirac_off)] * (1.f / 3.f) : coef[(size_t)l * I + i];
+      float v = weights ? c : W[(size_t)l * I + i] + c;
+      zs[l * 256 + threadIdx.x] = v;
+      n2 = fmaf(v, v, n2);
     }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int64_t i = ii[k];
-      if (i >= I) continue;
-      const float nrm = sqrtf(n2[k]);
-      if (weights) {
-        theta_out[i] = mu / (nrm + mu);
-        continue;
-      }
-      const float alpha = alpha_scale * theta[i];
-      const float fct = nrm > alpha ? alpha / nrm : 1.f;
-#pragma unroll
-      for (int l = 0; l < LMAX; ++l)
-        if (l < L) W[(size_t)l * I + i] = z[k][l] * fct;
+    const float nrm = sqrtf(n2);
+    if (weights) {
+      theta_out[i] = mu / (nrm + mu);
+      continue;
     }
+    const float alpha = alpha_scale * theta[i];
+    const float fct = nrm > alpha ? alpha / nrm : 1.f;
+#pragma unroll 16
+    for (int l = 0; l < L; ++l) W[(size_t)l * I + i] = zs[l * 256 + threadIdx.x] * fct;
   }
 }
 
@@ -322,7 +306,7 @@ struct SynFin2 {
 
 // Level 1 of all bases: the tiles of basis b + 1 are staged (cp.async) while basis b
 // is computed.
-__global__ void __launch_bounds__(256) k_synfin(SynFin2 s, float* __restrict__ A) {
+__global__ void __launch_bounds__(256, 4) k_synfin(SynFin2 s, float* __restrict__ A) {
   __shared__ float sh[2 * 4 * kTS2 + 2 * kT2 * (kKn2 + 1)];
   float* tcb[2] = {sh, sh + 4 * kTS2};
   float* lx = sh + 8 * kTS2;
@@ -406,9 +390,13 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
     const unsigned g = (unsigned)std::min<int64_t>((S.I + 255) / 256, 152 * 16);
     const float as = (float)(cb.mu / cb.kappa), mu = (float)cb.mu;
     const int wm = weights ? 1 : 0;
-    if (L <= 16) k_prox2<16><<<g, 256, 0, st>>>(W, coef, x, theta, theta_out, S.I, S.dirac_off, N, L, as, mu, wm);
-    else if (L <= 32) k_prox2<32><<<g, 256, 0, st>>>(W, coef, x, theta, theta_out, S.I, S.dirac_off, N, L, as, mu, wm);
-    else k_prox2<64><<<g, 256, 0, st>>>(W, coef, x, theta, theta_out, S.I, S.dirac_off, N, L, as, mu, wm);
+    const size_t smem = (size_t)L * 256 * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_prox2, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxL * 256 * (int)sizeof(float));
+      attr = true;
+    }
+    k_prox2<<<g, 256, smem, st>>>(W, coef, x, theta, theta_out, S.I, S.dirac_off, N, L, as, mu, wm);
     note_launches(1);
   }
   if (weights) return;

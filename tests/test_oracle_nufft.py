@@ -84,3 +84,30 @@ def test_scaling_is_inverse_kernel_transform():
     p = nu.pixel_coords(64)
     assert np.allclose(s * nu.kb_kernel_ft(2 * np.pi * p / 128), 1.0, rtol=1e-14)
     assert np.all(s > 0)
+
+
+@pytest.mark.parametrize("n1,n2", [(16, 16), (12, 20)])
+def test_sampled_measure_matches_fft_route_and_direct_dft(n1, n2):
+    """The FFT-free sampled evaluation equals G F Z x (numpy.fft route) to rounding and
+    the exact direct DFT to the interpolation error (Eq. 1)."""
+    rng = np.random.default_rng(11)
+    x = rng.random((n1, n2))
+    uv = rng.uniform(-np.pi, np.pi, size=(40, 2))
+    ys = nu.measure_sampled(x, uv)
+    yf = nu.measure(x, uv)
+    assert np.abs(ys - yf).max() <= 1e-11 * np.abs(yf).max()
+    yd = nu.direct_dft(x, uv)
+    assert np.linalg.norm(ys - yd) <= 1e-3 * np.linalg.norm(yd)
+
+
+def test_sampled_adjoint_matches_fft_route():
+    """Direct per-pixel summation of Re Phi^dagger v equals the gridding + inverse FFT route."""
+    rng = np.random.default_rng(12)
+    n1, n2 = 14, 18
+    uv = rng.uniform(-np.pi, np.pi, size=(60, 2))
+    v = rng.standard_normal(60) + 1j * rng.standard_normal(60)
+    full = nu.adjoint(v, uv, n1, n2).real
+    pix = [(0, 0), (3, 17), (13, 5), (7, 9)]
+    got = nu.adjoint_real_sampled(v, uv, n1, n2, pix)
+    want = np.array([full[r, c] for r, c in pix])
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(full).max()
