@@ -133,7 +133,10 @@ void launch_fft_adjoint(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, 
 void launch_fft_forward_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float2* grid, cudaStream_t st);
 void launch_fft_adjoint_fast(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta,
                              bool accumulate, cudaStream_t st);
-void launch_degrid(const Cube& cb, const float2* grid, float2* out, cudaStream_t st);
+void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st);
+int degrid_tiled_parts(const Cube& cb);
+void launch_degrid_pdfb_tiled(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
+                              float2* u_prev, double* partials, cudaStream_t st);
 void launch_degrid_pdfb(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
                         float2* u_prev, double* partials, int nparts, cudaStream_t st);
 int degrid_parts(const Cube& cb);

@@ -483,6 +483,7 @@ void alloc_scratch(fhs_ctx* ctx) {
     img = std::max(img, L * cb.n1 * cb.n2);
     vis = std::max(vis, (size_t)cb.n_vis);
     red = std::max(red, L * (size_t)degrid_parts(cb) * 2 * cb.B);
+    red = std::max(red, L * (size_t)degrid_tiled_parts(cb) * 2 * cb.B);
     red = std::max(red, L * 64 * 2);
     int nch = (cb.max_facet_pix + 1023) / 1024;
     gram = std::max(gram, (size_t)cb.facets.size() * nch * L * L);
@@ -584,9 +585,16 @@ void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
     sara_dual(ctx, cb, a.Xcheck, a.state.W, a.state.theta, A);
     // data fidelity: x_hat = F Z x, degrid + l2-ball duals, grid, adjoint
     launch_fft_forward(ctx, cb, a.X, ctx->s.grid, st);
-    int np = degrid_parts(cb);
-    launch_degrid_pdfb(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
-                       (float2*)a.state.u_prev, ctx->s.red, np, st);
+    int np;
+    if (use_fast(ctx, cb)) {
+      np = degrid_tiled_parts(cb);
+      launch_degrid_pdfb_tiled(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
+                               (float2*)a.state.u_prev, ctx->s.red, st);
+    } else {
+      np = degrid_parts(cb);
+      launch_degrid_pdfb(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
+                         (float2*)a.state.u_prev, ctx->s.red, np, st);
+    }
     launch_block_finalize(cb, ctx->s.red, np, ctx->s.blk_scale, stat + 2 * pp, st);
     adjoint_into(ctx, cb, ctx->s.vis, ctx->s.blk_scale, (float2*)a.state.v, A, cb.d_eta, true);
     launch_primal(cb, a.X, a.Xcheck, A, stat, pp, st);

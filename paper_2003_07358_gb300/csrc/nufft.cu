@@ -555,6 +555,122 @@ __global__ void __launch_bounds__(256) k_degrid_pdfb(const float2* __restrict__ 
   block_partials<8>(v0, v1, b, valid, B, sred, partials + ((size_t)l * nparts + blockIdx.x) * 2 * B);
 }
 
+// Tile-staged degridding (fast path).  One CTA per (grid tile, channel): every
+// visibility of the tile has its first tap in the tile, so its 7 x 7 footprint lies
+// in the (T + 6)^2 region starting at the tile corner, which is staged in shared
+// memory once (coalesced rows) and then read by all of the tile's visibilities.
+// Tiles with few visibilities read the grid directly instead.  MODE 0 stores
+// u = G x_hat; MODE 1 is the PDFB data step of k_degrid_pdfb with its per-block
+// partial sums accumulated per warp in shared memory over the tile (fixed order)
+// and written once per CTA: partials[l][tile][2][B].
+constexpr int kDegStageMin = 96;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__ grid, const float2* __restrict__ uv,
+                                                      const int32_t* __restrict__ tile_off,
+                                                      const int64_t* __restrict__ vis_off, VisGeom vg, int T,
+                                                      int ntr, int ntc, float2* __restrict__ out,
+                                                      const float2* __restrict__ y, const float2* __restrict__ v,
+                                                      float2* __restrict__ u_prev, const uint8_t* __restrict__ blk,
+                                                      int B, double* __restrict__ partials) {
+  extern __shared__ float2 sg[];
+  __shared__ double sacc[8][2][kMaxB];
+  const int l = blockIdx.y, tau = blockIdx.x;
+  const int tr = tau / ntc, tc = tau % ntc;
+  const int32_t* toff = tile_off + (size_t)l * (ntr * ntc * 4 + 1);
+  const int beg = toff[tau * 4], end = toff[tau * 4 + 4];
+  const int64_t vbase = vis_off[l];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (MODE == 1) {
+    for (int k = threadIdx.x; k < 8 * 2 * kMaxB; k += blockDim.x) (&sacc[0][0][0])[k] = 0.0;
+  }
+  const float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
+  const int R = T + kTaps - 1, SP = T + kTaps;      // staged side, odd row stride
+  const bool staged = end - beg >= kDegStageMin;
+  if (staged) {
+    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+      const int rr = idx / R, cc = idx - rr * R;
+      const int row = phys_row2((tr * T + rr) & (vg.K1 - 1), vg);
+      sg[rr * SP + cc] = gl[(size_t)row * vg.K2 + ((tc * T + cc) & (vg.K2 - 1))];
+    }
+  }
+  __syncthreads();
+  for (int base = beg; base < end; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const bool valid = k < end;
+    const int64_t i = vbase + k;
+    float2 u = make_float2(0.f, 0.f);
+    if (valid) {
+      const float2 w = uv[i];
+      float wc[kTaps], xr;
+      const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
+      const int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
+      const int lr = (kr & (vg.K1 - 1)) - tr * T, lc = (kc & (vg.K2 - 1)) - tc * T;
+      // the host sort puts the first tap in this tile; anything else reads the grid directly
+      if (staged && lr >= 0 && lr < T && lc >= 0 && lc < T) {
+        const float2* sp = sg + lr * SP + lc;
+#pragma unroll 1
+        for (int a = 0; a < kTaps; ++a) {
+          const float wra = kb_tap(a, xr);
+          float2 racc = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int b = 0; b < kTaps; ++b) {
+            const float2 g = sp[a * SP + b];
+            racc.x = fmaf(wc[b], g.x, racc.x);
+            racc.y = fmaf(wc[b], g.y, racc.y);
+          }
+          u.x = fmaf(wra, racc.x, u.x);
+          u.y = fmaf(wra, racc.y, u.y);
+        }
+      } else {
+        u = degrid_one(gl, w, vg);
+      }
+    }
+    if (MODE == 0) {
+      if (valid) out[i] = u;
+      continue;
+    }
+    double v0 = 0.0, v1 = 0.0;
+    int b = -1;
+    if (valid) {
+      const float2 yy = y[i], vv = v[i], up = u_prev[i];
+      const float2 z = make_float2(vv.x + 2.f * u.x - up.x, vv.y + 2.f * u.y - up.y);
+      const float2 d = make_float2(z.x - yy.x, z.y - yy.y);
+      out[i] = d;
+      u_prev[i] = u;
+      b = blk[i];
+      v0 = (double)fmaf(d.x, d.x, d.y * d.y);
+      const float rx = yy.x - u.x, ry = yy.y - u.y;
+      v1 = (double)fmaf(rx, rx, ry * ry);
+    }
+    // valid lanes form a prefix of the CTA, so lane 0 invalid means the warp is idle
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    if (b0 < 0) continue;
+    const bool uniform = __all_sync(0xffffffffu, b < 0 || b == b0);
+    for (int bb = uniform ? b0 : 0; bb < (uniform ? b0 + 1 : B); ++bb) {
+      double s0 = (b == bb) ? v0 : 0.0, s1 = (b == bb) ? v1 : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      if (lane == 0) {
+        sacc[wid][0][bb] += s0;
+        sacc[wid][1][bb] += s1;
+      }
+    }
+  }
+  if (MODE == 0) return;
+  __syncthreads();
+  double* po = partials + ((size_t)l * ntr * ntc + tau) * 2 * B;
+  for (int k = threadIdx.x; k < 2 * B; k += blockDim.x) {
+    const int c = k / B, bb = k - c * B;
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += sacc[w][c][bb];
+    po[k] = s;
+  }
+}
+
 // Partial sums of ||z - y||^2 per block and d = z - y (standalone l2-ball projection).
 __global__ void __launch_bounds__(256) k_l2ball_partials(const float2* __restrict__ z, const float2* __restrict__ y,
                                                          float2* __restrict__ d_out, const uint8_t* __restrict__ blk,
@@ -632,21 +748,26 @@ __global__ void k_l2ball_scale(const float2* __restrict__ d, const float* __rest
 // each visibility lands in exactly one (tile, pass).
 // Class order within a tile: 0 interior, 1 crosses down only, 2 crosses down
 // and right, 3 crosses right only.
-// Accumulation is in fixed point with integer shared-memory atomics (much faster
-// than floating-point ones, and order-independent, so the result is bitwise
-// deterministic).  A first sweep over the CTA's visibilities gives
-// bound = max(sum |Re val|, sum |Im val|) >= |any cell sum| (Kaiser-Bessel weights
-// are <= 1); values are scaled by S = 2^e with bound * S < 2^(bits - 3) and rounded to
-// integers, so nothing can overflow, and the cell is read back as acc / S.
-template <typename Acc> struct FixedAcc;
-template <> struct FixedAcc<int> {
-  static constexpr int kBits = 32;
-  __device__ static void add(int* p, float v) { atomicAdd(p, __float2int_rn(v)); }
-};
-template <> struct FixedAcc<long long> {
-  static constexpr int kBits = 64;
-  __device__ static void add(long long* p, float v) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__float2ll_rn(v));
+// Accumulation is in two-word fixed point with 32-bit integer shared-memory atomics
+// (several times faster than floating-point ones, and order-independent, so the
+// result is bitwise deterministic).  A first sweep over the CTA's visibilities
+// gives n (their count) and bound = max(sum |Re val|, sum |Im val|) >= |any cell
+// sum| (Kaiser-Bessel weights are <= 1).  Each contribution c, scaled by S = 2^e with
+// bound * S < 2^21, is split exactly into hi = rint(c S) and the residual
+// r = c S - hi, |r| <= 1/2, stored as lo = rint(r 2^k) with n 2^(k-1) < 2^30; neither
+// word can overflow, and the cell is read back as ((hi << k) + lo) / (S 2^k), a
+// resolution of about 2^-(21 + k) of the bound.  Both roundings use the
+// 1.5 * 2^23 magic-number addition (exact for |x| < 2^22).
+struct FixedSplit {
+  static constexpr float kMagic = 12582912.f;         // 1.5 * 2^23
+  static constexpr int kMagicBits = 0x4B400000;
+  __device__ static void add(int* hi, int* lo, float c, float two_k) {
+    const float t = __fadd_rn(c, kMagic);
+    const float ch = __fsub_rn(t, kMagic);              // rint(c), exact
+    const float r = __fsub_rn(c, ch);                   // exact residual
+    const float t2 = __fmaf_rn(r, two_k, kMagic);
+    atomicAdd(hi, __float_as_int(t) - kMagicBits);
+    atomicAdd(lo, __float_as_int(t2) - kMagicBits);
   }
 };
 
@@ -663,28 +784,31 @@ __device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, i
   else { beg = toff[sidx + 2]; end = toff[sidx + 3]; }                  // crosses both: class 2
 }
 
-template <typename Acc>
 __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
                                               float2* __restrict__ v_write, const float2* __restrict__ uv,
                                               const uint8_t* __restrict__ blk, const int32_t* __restrict__ tile_off,
                                               const int64_t* __restrict__ vis_off, float2* __restrict__ grid,
                                               VisGeom vg, int T, int ntr, int ntc, int B) {
-  extern __shared__ __align__(16) unsigned char sraw[];
+  extern __shared__ int sacc_i[];
   __shared__ float sbound[2][8];
-  Acc* are = reinterpret_cast<Acc*>(sraw);
   const int TP = T + 1;                  // padded row stride: banks (row + col) mod 32
-  Acc* aim = are + T * TP;
+  int* rhi = sacc_i;                     // [4][T][TP]: Re hi, Im hi, Re lo, Im lo
+  int* ihi = rhi + T * TP;
+  int* rlo = ihi + T * TP;
+  int* ilo = rlo + T * TP;
   const int l = blockIdx.y;
   const int tau = blockIdx.x;
   const int tr = tau / ntc, tc = tau % ntc;
-  for (int k = threadIdx.x; k < 2 * T * TP; k += blockDim.x) are[k] = 0;
+  for (int k = threadIdx.x; k < 4 * T * TP; k += blockDim.x) sacc_i[k] = 0;
   const int64_t vbase = vis_off[l];
   const int32_t* toff = tile_off + (size_t)l * (ntr * ntc * 4 + 1);
   // sweep 1: bound on any cell of this tile
   float bx = 0.f, by = 0.f;
+  int cnt = 0;
   for (int pass = 0; pass < 4; ++pass) {
     int sr, sc, beg, end;
     grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
+    cnt += end - beg;
     for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
       const int64_t i = vbase + k;
       float2 val = vals[i];
@@ -706,11 +830,15 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
   float bound = 0.f;
 #pragma unroll
   for (int w = 0; w < 8; ++w) bound = fmaxf(bound, fmaxf(sbound[0][w], sbound[1][w]));
-  // S = 2^e, bound * S < 2^(bits - 3); the 1.01 covers the rounding of the FP32 sum
-  // (ex from the exponent field: bound * 1.01 < 2^ex; zero or subnormal bound gives ex = -126)
+  // S = 2^e with bound * S < 2^21 (ex from the exponent field: bound * 1.01 < 2^ex;
+  // the 1.01 covers the rounding of the FP32 sums; zero or subnormal bound gives -126)
   const int ex = (int)((__float_as_uint(bound * 1.01f) >> 23) & 0xffu) - 126;
-  const int e = min(FixedAcc<Acc>::kBits - 3 - ex, 120);
-  const float S = __uint_as_float((unsigned)(e + 127) << 23), invS = __uint_as_float((unsigned)(127 - e) << 23);
+  const int e = min(21 - ex, 100);
+  // ksh with cnt * 2^(ksh - 1) < 2^30 (cnt: visibilities of the 4 passes, each adds at
+  // most once to a cell), at most 22 for the magic-number rounding
+  const int ksh = max(0, min(22, 30 - (32 - __clz(cnt))));
+  const float S = __uint_as_float((unsigned)(e + 127) << 23);
+  const float two_k = __uint_as_float((unsigned)(ksh + 127) << 23);
   // sweep 2: taps
   for (int pass = 0; pass < 4; ++pass) {
     const int dr = pass >> 1, dc = pass & 1;
@@ -747,25 +875,29 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
 #pragma unroll
         for (int b = 0; b < kTaps; ++b) {
           if (b < b0 || b >= b1) continue;
-          FixedAcc<Acc>::add(&are[rowoff + b], wc[b] * va);
-          FixedAcc<Acc>::add(&aim[rowoff + b], wc[b] * vb);
+          FixedSplit::add(&rhi[rowoff + b], &rlo[rowoff + b], wc[b] * va, two_k);
+          FixedSplit::add(&ihi[rowoff + b], &ilo[rowoff + b], wc[b] * vb, two_k);
         }
       }
     }
   }
   __syncthreads();
   float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
-  for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
-    int rr = k / T, cc = k % T;
-    int row = phys_row2(tr * T + rr, vg);
+  // value = ((hi << ksh) + lo) 2^-(e + ksh): exact in int64, one rounding to float,
+  // then two power-of-two scalings (exact unless the result is subnormal)
+  const float inv_e = __uint_as_float((unsigned)(127 - e) << 23);
+  const float inv_k = __uint_as_float((unsigned)(127 - ksh) << 23);
+  for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
+    const int rr = q / T, cc = q % T, o = rr * TP + cc;
+    const long long vr = ((long long)rhi[o] << ksh) + rlo[o];
+    const long long vi = ((long long)ihi[o] << ksh) + ilo[o];
+    const int row = phys_row2(tr * T + rr, vg);
     gl[(size_t)row * vg.K2 + tc * T + cc] =
-        make_float2((float)are[rr * TP + cc] * invS, (float)aim[rr * TP + cc] * invS);
+        make_float2((float)vr * inv_k * inv_e, (float)vi * inv_k * inv_e);
   }
 }
 
 // ------------------------------------------------------------- launchers
-using kGridAcc = long long;            // fixed-point accumulator of the gridder
-
 static VisGeom vis_geom(const Cube& cb) {
   VisGeom vg;
   vg.K1 = cb.K1; vg.K2 = cb.K2; vg.N1c = cb.N1c; vg.N2c = cb.N2c;
@@ -777,9 +909,31 @@ static VisGeom vis_geom(const Cube& cb) {
 
 int degrid_parts(const Cube& cb) { return (int)((cb.max_M + 255) / 256); }
 
-void launch_degrid(const Cube& cb, const float2* grid, float2* out, cudaStream_t st) {
-  dim3 grd(degrid_parts(cb), cb.L);
-  k_degrid<<<grd, 256, 0, st>>>(grid, cb.d_uv, out, cb.d_vis_off, vis_geom(cb));
+int degrid_tiled_parts(const Cube& cb) { return cb.ntile_r * cb.ntile_c; }
+
+static size_t degrid_tiled_smem(const Cube& cb) {
+  return (size_t)(cb.tile + kTaps - 1) * (cb.tile + kTaps) * sizeof(float2);
+}
+
+void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st) {
+  if (tiled) {
+    dim3 grd(degrid_tiled_parts(cb), cb.L);
+    k_degrid_tiled<0><<<grd, 256, degrid_tiled_smem(cb), st>>>(grid, cb.d_uv, cb.d_tile_off, cb.d_vis_off,
+                                                               vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, out,
+                                                               nullptr, nullptr, nullptr, nullptr, cb.B, nullptr);
+  } else {
+    dim3 grd(degrid_parts(cb), cb.L);
+    k_degrid<<<grd, 256, 0, st>>>(grid, cb.d_uv, out, cb.d_vis_off, vis_geom(cb));
+  }
+  note_launches(1);
+}
+
+void launch_degrid_pdfb_tiled(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
+                              float2* u_prev, double* partials, cudaStream_t st) {
+  dim3 grd(degrid_tiled_parts(cb), cb.L);
+  k_degrid_tiled<1><<<grd, 256, degrid_tiled_smem(cb), st>>>(grid, cb.d_uv, cb.d_tile_off, cb.d_vis_off,
+                                                             vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, d_out, y,
+                                                             v, u_prev, cb.d_blk, cb.B, partials);
   note_launches(1);
 }
 
@@ -813,13 +967,12 @@ void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, fl
 
 void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write, float2* grid,
                  cudaStream_t st) {
-  using Acc = kGridAcc;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k_grid<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
+  if (!attr) { cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
-  size_t sm = 2 * (size_t)cb.tile * (cb.tile + 1) * sizeof(Acc);
-  k_grid<Acc><<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
-                                    vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
+  size_t sm = 4 * (size_t)cb.tile * (cb.tile + 1) * sizeof(int);
+  k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
+                               vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
 }
 
@@ -848,7 +1001,7 @@ void launch_vis_scatter(const int64_t* perm, int64_t n, const float2* in, float2
 
 void launch_measure(fhs_ctx* ctx, const Cube& cb, const float* x, float2* y, cudaStream_t st) {
   launch_fft_forward(ctx, cb, x, ctx->s.grid, st);
-  launch_degrid(cb, ctx->s.grid, y, st);
+  launch_degrid(cb, ctx->s.grid, y, ctx->path == FHS_PATH_FAST, st);
 }
 
 // host-side replica of kb_weights' first-tap rule (exact same float operations)

@@ -173,17 +173,23 @@ constexpr int kTS2 = kKn2 * (kKn2 + 1);             // one staged band
 template <int F>
 __device__ __forceinline__ void syn2_stage(const Syn2& s, int l, int r0, int c0, float* tc) {
   constexpr int KN = kT2 / 2 + F / 2;
-  const int klo = r0 / 2, clo = c0 / 2;
-  const float* Wl = s.W + (size_t)l * s.I;
-  const float* lll = s.ll ? s.ll + (size_t)l * s.mo1 * s.mo2 : nullptr;
-  for (int idx = threadIdx.x; idx < 4 * KN * KN; idx += 256) {
-    int band = idx / (KN * KN), rem = idx - band * (KN * KN);
-    int kr = rem / KN, kc = rem - kr * KN;
-    int gk = klo + kr, gc = clo + kc;
-    bool v = gk < s.mo1 && gc < s.mo2;
-    int64_t pos = v ? (int64_t)gk * s.mo2 + gc : 0;
-    const float* src = band == 0 ? (lll ? lll + pos : Wl + s.off[3] + pos) : Wl + s.off[band - 1] + pos;
-    cp_async4(&tc[band * kTS2 + kr * (kKn2 + 1) + kc], src, v);
+  static_assert(KN <= 32, "one warp spans a staged row");
+  const int kc = threadIdx.x & 31, kr0 = threadIdx.x >> 5;   // lane = column, warp = row (step 8)
+  if (kc < KN) {
+    const int klo = r0 / 2, gc = c0 / 2 + kc;
+    const bool vc = gc < s.mo2;
+    const float* Wl = s.W + (size_t)l * s.I;
+    const float* b0 = s.ll ? s.ll + (size_t)l * s.mo1 * s.mo2 : Wl + s.off[3];
+    const float* bp[4] = {b0, Wl + s.off[0], Wl + s.off[1], Wl + s.off[2]};
+#pragma unroll
+    for (int band = 0; band < 4; ++band) {
+#pragma unroll
+      for (int kr = kr0; kr < KN; kr += 8) {
+        const int gk = klo + kr;
+        const bool v = vc && gk < s.mo1;
+        cp_async4(&tc[band * kTS2 + kr * (kKn2 + 1) + kc], bp[band] + (v ? (int64_t)gk * s.mo2 + gc : 0), v);
+      }
+    }
   }
   cp_async_commit();
 }
@@ -204,25 +210,28 @@ __device__ __forceinline__ void syn2_compute(const float* tc, float* lx, float* 
 #pragma unroll
     for (int u = 0; u <= WIN; ++u) {
       const int o = (mg + u) * (kKn2 + 1) + kc;
-      vl[u] = tc[o] * ll_scale;
-      v0[u] = tc[kTS2 + o] * third;
-      v1[u] = tc[2 * kTS2 + o] * third;
-      v2[u] = tc[3 * kTS2 + o] * third;
+      vl[u] = tc[o];
+      v0[u] = tc[kTS2 + o];
+      v1[u] = tc[2 * kTS2 + o];
+      v2[u] = tc[3 * kTS2 + o];
     }
+    // raw coefficients; the dictionary's 1/3 (and ll_scale) applied once per output
 #pragma unroll
     for (int mm = 0; mm < 2; ++mm) {
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        float sl = 0.f, sx = 0.f;
+        float slh = 0.f, slg = 0.f, sxh = 0.f, sxg = 0.f;
 #pragma unroll
         for (int q = 0; q < F / 2; ++q) {
           const float hh = f.h[2 * q + 1 - p], gg = f.g[2 * q + 1 - p];
-          sl = fmaf(hh, vl[mm + q], fmaf(gg, v1[mm + q], sl));
-          sx = fmaf(hh, v0[mm + q], fmaf(gg, v2[mm + q], sx));
+          slh = fmaf(hh, vl[mm + q], slh);
+          slg = fmaf(gg, v1[mm + q], slg);
+          sxh = fmaf(hh, v0[mm + q], sxh);
+          sxg = fmaf(gg, v2[mm + q], sxg);
         }
         const int il = 2 * (mg + mm) + p;
-        lx[il * (kKn2 + 1) + kc] = sl;
-        hx[il * (kKn2 + 1) + kc] = sx;
+        lx[il * (kKn2 + 1) + kc] = fmaf(ll_scale, slh, third * slg);
+        hx[il * (kKn2 + 1) + kc] = third * (sxh + sxg);
       }
     }
   }
