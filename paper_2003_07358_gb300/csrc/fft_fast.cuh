@@ -187,6 +187,15 @@ static void row2_n(const Cube& cb, float2* grid, int inv, const float2* tw, int 
 
 template <int N>
 static void colA_fwd_n(const Cube& cb, const float* x, float2* grid, const float2* tw, int Kmax, cudaStream_t st) {
+  if constexpr (N >= 64 && N <= 256) {
+    static bool attr_r = false;
+    if (!attr_r) { cudaFuncSetAttribute(k_colA_fwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegCol<N>::SMEM); attr_r = true; }
+    dim3 grd((cb.n2 + 31) / 32, cb.N2c, cb.L);
+    k_colA_fwd_r<N><<<grd, 256, RegCol<N>::SMEM, st>>>(x, grid, cb.d_scale_r, cb.d_scale_c, cb.n1, cb.n2, cb.K1,
+                                                       cb.K2, cb.N2c, tw, Kmax / N, Kmax / cb.K1);
+    note_launches(1);
+    return;
+  }
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_colA_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
   constexpr int W = ColCfg<N>::W;
@@ -196,8 +205,22 @@ static void colA_fwd_n(const Cube& cb, const float* x, float2* grid, const float
   note_launches(1);
 }
 
+template <int N, bool INV>
+static void colB_r_n(const Cube& cb, float2* grid, const float2* tw, int Kmax, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_colB_r<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegCol<N>::SMEM); attr = true; }
+  dim3 grd((cb.n2 + 31) / 32, cb.N1c, cb.L);
+  k_colB_r<N, INV><<<grd, 256, RegCol<N>::SMEM, st>>>(grid, cb.n2, cb.K1, cb.K2, tw, Kmax / N);
+  note_launches(1);
+}
+
 template <int N>
 static void colB_n(const Cube& cb, float2* grid, int inv, const float2* tw, int Kmax, cudaStream_t st) {
+  if constexpr (N >= 64 && N <= 256) {
+    if (inv) colB_r_n<N, true>(cb, grid, tw, Kmax, st);
+    else colB_r_n<N, false>(cb, grid, tw, Kmax, st);
+    return;
+  }
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_colB<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
   constexpr int W = ColCfg<N>::W;
@@ -209,6 +232,15 @@ static void colB_n(const Cube& cb, float2* grid, int inv, const float2* tw, int 
 template <int N>
 static void colA_adj_n(const Cube& cb, const float2* grid, float* out, const float* eta, bool acc, const float2* tw,
                        int Kmax, cudaStream_t st) {
+  if constexpr (N >= 64 && N <= 256) {
+    static bool attr_r = false;
+    if (!attr_r) { cudaFuncSetAttribute(k_colA_adj_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegCol<N>::SMEM); attr_r = true; }
+    dim3 grd((cb.n2 + 31) / 32, cb.N2c, cb.L);
+    k_colA_adj_r<N><<<grd, 256, RegCol<N>::SMEM, st>>>(grid, out, cb.d_scale_r, cb.d_scale_c, eta, acc ? 1 : 0, cb.n1,
+                                                       cb.n2, cb.K1, cb.K2, cb.N2c, tw, Kmax / N, Kmax / cb.K1);
+    note_launches(1);
+    return;
+  }
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_colA_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
   constexpr int W = ColCfg<N>::W;

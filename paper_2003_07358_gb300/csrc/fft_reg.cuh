@@ -171,3 +171,128 @@ __global__ void __launch_bounds__(RegRow<N>::NT, 2) k_rowr(float2* __restrict__ 
     }
   }
 }
+
+// ------------------------------------------------------------------ columns
+// Register-resident column DFT of length N = R1 * 8 (64, 128, 256) over 32 adjacent
+// grid columns (one per lane) and 8 row groups (one per warp):
+//   i = i0 + 8 m (i0 = warp, m < R1),  k = k_m + R1 k_i;
+//   pass 1: R1-point DFT over m of the thread's column, times w_N^{i0 k_m};
+//   pass 2: tasks k_m (warp-strided), 8-point DFT over i0.
+// One exchange through a [R1][8][32] float2 buffer (lanes = columns: conflict-free).
+// load(i) returns element i of the thread's column; store(k, v) writes output k.
+template <int N> struct RegCol {
+  static constexpr int R1 = N / 8;
+  static constexpr int SMEM = N * 32 * (int)sizeof(float2);
+};
+
+template <int N, bool INV, class Load, class Store>
+__device__ __forceinline__ void col_fft_reg(float2* sm, const float2* __restrict__ tw, int twstride, Load load,
+                                            Store store) {
+  constexpr int R1 = RegCol<N>::R1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  {
+    float2 v[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) v[m] = load(w + 8 * m);
+    rdft<R1, INV>(v);
+#pragma unroll
+    for (int km = 1; km < R1; ++km) {
+      float2 t = __ldg(&tw[(size_t)((w * km) & (N - 1)) * twstride]);
+      if (INV) t.y = -t.y;
+      v[km] = cmul(v[km], t);
+    }
+#pragma unroll
+    for (int km = 0; km < R1; ++km) sm[(km * 8 + w) * 32 + lane] = v[km];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int km = w; km < R1; km += 8) {
+    float2 z[8];
+#pragma unroll
+    for (int i0 = 0; i0 < 8; ++i0) z[i0] = sm[(km * 8 + i0) * 32 + lane];
+    rdft<8, INV>(z);
+#pragma unroll
+    for (int ki = 0; ki < 8; ++ki) store(km + R1 * ki, z[ki]);
+  }
+}
+
+// Step A forward (Z fused) for group g, image columns c0 .. c0 + 31 (see k_colA_fwd).
+template <int N>
+__global__ void __launch_bounds__(256) k_colA_fwd_r(const float* __restrict__ x, float2* __restrict__ grid,
+                                                    const float* __restrict__ sr, const float* __restrict__ sc,
+                                                    int n1, int n2, int K1, int K2, int N2c,
+                                                    const float2* __restrict__ tw, int twN, int twK) {
+  extern __shared__ float2 sm[];
+  const int l = blockIdx.z, g = blockIdx.y, cc = blockIdx.x * 32 + (threadIdx.x & 31);
+  const float* xl = x + (size_t)l * n1 * n2;
+  float2* gl = grid + (size_t)l * K1 * K2;
+  const int h1 = n1 / 2, h2 = n2 / 2;
+  const bool col_ok = cc < n2;
+  const int c = cc < h2 ? cc + h2 : cc - h2;
+  const float scc = col_ok ? sc[c] : 0.f;
+  const int gcol = colmap(cc, n2, K2);
+  auto load = [&](int i) {
+    const int rho = N2c * i + g;
+    const int r = rho < h1 ? rho + h1 : (rho >= K1 - h1 ? rho - (K1 - h1) : -1);
+    float val = 0.f;
+    if (r >= 0 && col_ok) val = xl[(size_t)r * n2 + c] * sr[r] * scc;
+    return make_float2(val, 0.f);
+  };
+  auto store = [&](int k, float2 v) {
+    if (!col_ok) return;
+    if (N2c > 1) v = cmul(v, __ldg(&tw[(size_t)(g * k) * twK]));
+    gl[(size_t)(N2c * k + g) * K2 + gcol] = v;
+  };
+  col_fft_reg<N, false>(sm, tw, twN, load, store);
+}
+
+// Step B (both directions): group k1, rows N k1 + i (see k_colB).
+template <int N, bool INV>
+__global__ void __launch_bounds__(256) k_colB_r(float2* __restrict__ grid, int n2, int K1, int K2,
+                                                const float2* __restrict__ tw, int twN) {
+  extern __shared__ float2 sm[];
+  const int l = blockIdx.z, k1 = blockIdx.y, cc = blockIdx.x * 32 + (threadIdx.x & 31);
+  float2* gl = grid + (size_t)l * K1 * K2 + (size_t)N * k1 * K2;
+  const bool col_ok = cc < n2;
+  const int gcol = colmap(cc, n2, K2);
+  auto load = [&](int i) { return col_ok ? gl[(size_t)i * K2 + gcol] : make_float2(0.f, 0.f); };
+  auto store = [&](int k, float2 v) {
+    if (col_ok) gl[(size_t)k * K2 + gcol] = v;
+  };
+  col_fft_reg<N, INV>(sm, tw, twN, load, store);
+}
+
+// Step A^H with the crop fused (see k_colA_adj).
+template <int N>
+__global__ void __launch_bounds__(256) k_colA_adj_r(const float2* __restrict__ grid, float* __restrict__ out,
+                                                    const float* __restrict__ sr, const float* __restrict__ sc,
+                                                    const float* __restrict__ eta, int accumulate, int n1, int n2,
+                                                    int K1, int K2, int N2c, const float2* __restrict__ tw, int twN,
+                                                    int twK) {
+  extern __shared__ float2 sm[];
+  const int l = blockIdx.z, g = blockIdx.y, cc = blockIdx.x * 32 + (threadIdx.x & 31);
+  const float2* gl = grid + (size_t)l * K1 * K2;
+  const bool col_ok = cc < n2;
+  const int gcol = colmap(cc, n2, K2);
+  const int h1 = n1 / 2, h2 = n2 / 2;
+  const int c = cc < h2 ? cc + h2 : cc - h2;
+  const float e = (eta ? eta[l] : 1.f) * (col_ok ? sc[c] : 0.f);
+  float* ol = out + (size_t)l * n1 * n2;
+  auto load = [&](int i) {
+    float2 v = make_float2(0.f, 0.f);
+    if (col_ok) {
+      v = gl[(size_t)(N2c * i + g) * K2 + gcol];
+      if (N2c > 1) v = cmul(v, cconj(__ldg(&tw[(size_t)(g * i) * twK])));
+    }
+    return v;
+  };
+  auto store = [&](int k, float2 v) {
+    const int rho = N2c * k + g;
+    const int r = rho < h1 ? rho + h1 : (rho >= K1 - h1 ? rho - (K1 - h1) : -1);
+    if (r < 0 || !col_ok) return;
+    const float val = e * sr[r] * v.x;
+    const size_t o = (size_t)r * n2 + c;
+    ol[o] = accumulate ? ol[o] + val : val;
+  };
+  col_fft_reg<N, true>(sm, tw, twN, load, store);
+}
