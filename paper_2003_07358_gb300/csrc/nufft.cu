@@ -748,28 +748,18 @@ __global__ void k_l2ball_scale(const float2* __restrict__ d, const float* __rest
 // each visibility lands in exactly one (tile, pass).
 // Class order within a tile: 0 interior, 1 crosses down only, 2 crosses down
 // and right, 3 crosses right only.
-// Accumulation is in two-word fixed point with 32-bit integer shared-memory atomics
-// (several times faster than floating-point ones, and order-independent, so the
-// result is bitwise deterministic).  A first sweep over the CTA's visibilities
-// gives n (their count) and bound = max(sum |Re val|, sum |Im val|) >= |any cell
-// sum| (Kaiser-Bessel weights are <= 1).  Each contribution c, scaled by S = 2^e with
-// bound * S < 2^21, is split exactly into hi = rint(c S) and the residual
-// r = c S - hi, |r| <= 1/2, stored as lo = rint(r 2^k) with n 2^(k-1) < 2^30; neither
-// word can overflow, and the cell is read back as ((hi << k) + lo) / (S 2^k), a
-// resolution of about 2^-(21 + k) of the bound.  Both roundings use the
-// 1.5 * 2^23 magic-number addition (exact for |x| < 2^22).
-struct FixedSplit {
-  static constexpr float kMagic = 12582912.f;         // 1.5 * 2^23
-  static constexpr int kMagicBits = 0x4B400000;
-  __device__ static void add(int* hi, int* lo, float c, float two_k) {
-    const float t = __fadd_rn(c, kMagic);
-    const float ch = __fsub_rn(t, kMagic);              // rint(c), exact
-    const float r = __fsub_rn(c, ch);                   // exact residual
-    const float t2 = __fmaf_rn(r, two_k, kMagic);
-    atomicAdd(hi, __float_as_int(t) - kMagicBits);
-    atomicAdd(lo, __float_as_int(t2) - kMagicBits);
-  }
-};
+// Accumulation is in fixed point with 32-bit integer shared-memory atomics (several
+// times faster than floating-point ones, and order-independent, so the result is
+// bitwise deterministic), with one scale per 8 x 8 sub-block of the tile:
+//   sweep 0: m = max over the CTA's visibilities of max(|Re v|, |Im v|);
+//   sweep 1: every visibility adds q = ceil(max(|Re v|, |Im v|) 2^qb / m) (an integer
+//            upper bound of its magnitude) to the sub-blocks its 7 x 7 footprint
+//            touches in this tile (qb chosen so that no counter can overflow);
+//   then bound_sb = sum q * m / 2^qb >= |any cell sum of the sub-block| (Kaiser-Bessel
+//   weights are <= 1) and S_sb = 2^e with bound_sb * S_sb < 2^29;
+//   sweep 2: each tap adds rint(c S_sb) to its cell; the cell is read back as
+//            acc / S_sb (resolution 2^-29 of its sub-block's bound).
+constexpr int kGridSB = 8;                        // sub-block side (cells)
 
 // Source range [beg, end) of pass (dr, dc) for destination tile (tr, tc).
 __device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, int tr, int tc, int ntr, int ntc,
@@ -784,26 +774,30 @@ __device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, i
   else { beg = toff[sidx + 2]; end = toff[sidx + 3]; }                  // crosses both: class 2
 }
 
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((unsigned)(e + 127) << 23); }
+
 __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
                                               float2* __restrict__ v_write, const float2* __restrict__ uv,
                                               const uint8_t* __restrict__ blk, const int32_t* __restrict__ tile_off,
                                               const int64_t* __restrict__ vis_off, float2* __restrict__ grid,
                                               VisGeom vg, int T, int ntr, int ntc, int B) {
   extern __shared__ int sacc_i[];
-  __shared__ float sbound[2][8];
+  __shared__ float sred[8];
+  __shared__ int sbq[(kGridTile / kGridSB) * (kGridTile / kGridSB)];
+  __shared__ float sbS[(kGridTile / kGridSB) * (kGridTile / kGridSB)];
   const int TP = T + 1;                  // padded row stride: banks (row + col) mod 32
-  int* rhi = sacc_i;                     // [4][T][TP]: Re hi, Im hi, Re lo, Im lo
-  int* ihi = rhi + T * TP;
-  int* rlo = ihi + T * TP;
-  int* ilo = rlo + T * TP;
+  const int NSB = (T + kGridSB - 1) / kGridSB;      // sub-blocks per side
+  int* are = sacc_i;
+  int* aim = are + T * TP;
   const int l = blockIdx.y;
   const int tau = blockIdx.x;
   const int tr = tau / ntc, tc = tau % ntc;
-  for (int k = threadIdx.x; k < 4 * T * TP; k += blockDim.x) sacc_i[k] = 0;
+  for (int k = threadIdx.x; k < 2 * T * TP; k += blockDim.x) sacc_i[k] = 0;
+  for (int k = threadIdx.x; k < NSB * NSB; k += blockDim.x) sbq[k] = 0;
   const int64_t vbase = vis_off[l];
   const int32_t* toff = tile_off + (size_t)l * (ntr * ntc * 4 + 1);
-  // sweep 1: bound on any cell of this tile
-  float bx = 0.f, by = 0.f;
+  // ---- sweep 0: largest component magnitude and visibility count
+  float m = 0.f;
   int cnt = 0;
   for (int pass = 0; pass < 4; ++pass) {
     int sr, sc, beg, end;
@@ -811,35 +805,62 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
     cnt += end - beg;
     for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
       const int64_t i = vbase + k;
-      float2 val = vals[i];
+      const float2 val = vals[i];
       const float s = blk_scale ? blk_scale[l * B + blk[i]] : 1.f;
-      bx += fabsf(val.x * s);
-      by += fabsf(val.y * s);
+      m = fmaxf(m, fmaxf(fabsf(val.x * s), fabsf(val.y * s)));
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    bx += __shfl_xor_sync(0xffffffffu, bx, o);
-    by += __shfl_xor_sync(0xffffffffu, by, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    sbound[0][threadIdx.x >> 5] = bx;
-    sbound[1][threadIdx.x >> 5] = by;
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) m = fmaxf(m, sred[w]);
+  // qb: cnt * (2^qb + 1) < 2^30, so no counter can overflow (q <= 2^qb + 1 with the
+  // rounding of |v| / m); a tile without signal keeps every scale at 1
+  const int qb = max(0, min(20, 29 - (32 - __clz(cnt))));
+  const bool any = m > 1e-30f;
+  const float qscale = any ? pow2f(qb) / m : 0.f;
+  // ---- sweep 1: per sub-block upper bounds (integer, order-independent)
+  if (any) {
+    for (int pass = 0; pass < 4; ++pass) {
+      const int dr = pass >> 1, dc = pass & 1;
+      int sr, sc, beg, end;
+      grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
+      for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
+        const int64_t i = vbase + k;
+        const float2 w = uv[i];
+        const float2 val = vals[i];
+        const float s = blk_scale ? blk_scale[l * B + blk[i]] : 1.f;
+        const int q = (int)ceilf(fmaxf(fabsf(val.x * s), fabsf(val.y * s)) * qscale);
+        float xr, xc;
+        const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
+        const int kc = kb_first(w.x, vg.tc.hi_c, vg.tc.lo_c, xc);
+        const int lr = (kr & (vg.K1 - 1)) - sr * T - dr * T;
+        const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
+        if (lr >= T || lc >= T || lr + kTaps <= 0 || lc + kTaps <= 0) continue;   // no tap here
+        const int r0 = max(lr, 0) / kGridSB, r1 = min(lr + kTaps - 1, T - 1) / kGridSB;
+        const int c0 = max(lc, 0) / kGridSB, c1 = min(lc + kTaps - 1, T - 1) / kGridSB;
+        for (int br = r0; br <= r1; ++br)
+          for (int bc = c0; bc <= c1; ++bc) atomicAdd(&sbq[br * NSB + bc], q);
+      }
+    }
   }
   __syncthreads();
-  float bound = 0.f;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) bound = fmaxf(bound, fmaxf(sbound[0][w], sbound[1][w]));
-  // S = 2^e with bound * S < 2^21 (ex from the exponent field: bound * 1.01 < 2^ex;
-  // the 1.01 covers the rounding of the FP32 sums; zero or subnormal bound gives -126)
-  const int ex = (int)((__float_as_uint(bound * 1.01f) >> 23) & 0xffu) - 126;
-  const int e = min(21 - ex, 100);
-  // ksh with cnt * 2^(ksh - 1) < 2^30 (cnt: visibilities of the 4 passes, each adds at
-  // most once to a cell), at most 22 for the magic-number rounding
-  const int ksh = max(0, min(22, 30 - (32 - __clz(cnt))));
-  const float S = __uint_as_float((unsigned)(e + 127) << 23);
-  const float two_k = __uint_as_float((unsigned)(ksh + 127) << 23);
-  // sweep 2: taps
+  for (int k = threadIdx.x; k < NSB * NSB; k += blockDim.x) {
+    float S = 1.f;
+    if (any && sbq[k] > 0) {
+      // bound = sbq m / 2^qb (the 1.01 covers the roundings of q and of this product;
+      // an overflow to infinity only makes S small); S = 2^e with bound S < 2^29
+      const float bnd = (float)sbq[k] * m * pow2f(-qb) * 1.01f;
+      const int eb = (int)((__float_as_uint(bnd) >> 23) & 0xffu) - 126;   // bnd < 2^eb
+      S = pow2f(max(-100, min(29 - eb, 100)));
+    }
+    sbS[k] = S;
+  }
+  __syncthreads();
+  // ---- sweep 2: taps
   for (int pass = 0; pass < 4; ++pass) {
     const int dr = pass >> 1, dc = pass & 1;
     int sr, sc, beg, end;
@@ -863,37 +884,36 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
       const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
       const int a0 = max(0, -lr), a1 = min(kTaps, T - lr);
       const int b0 = max(0, -lc), b1 = min(kTaps, T - lc);
-      const float vx = val.x * S, vy = val.y * S;
-      // rolled, warp-uniform row loop (the row weight is evaluated in the loop) keeps
-      // the register count low; the 7 column weights stay in registers
+      // the footprint spans at most two sub-block columns: b < bsplit -> first
+      const int c0 = min(max(lc, 0) / kGridSB, NSB - 1);
+      const int bsplit = (c0 + 1) * kGridSB - lc;
 #pragma unroll 1
       for (int a = 0; a < kTaps; ++a) {
         if (a < a0 || a >= a1) continue;
         const float wa = kb_tap(a, xr);
-        const int rowoff = (lr + a) * TP + lc;
-        const float va = wa * vx, vb = wa * vy;
+        const int rr = lr + a;
+        const int rowoff = rr * TP + lc;
+        const int sbr = (rr / kGridSB) * NSB;
+        const float S0 = sbS[sbr + c0], S1 = sbS[sbr + min(c0 + 1, NSB - 1)];
+        const float va0 = wa * val.x * S0, vb0 = wa * val.y * S0;
+        const float va1 = wa * val.x * S1, vb1 = wa * val.y * S1;
 #pragma unroll
         for (int b = 0; b < kTaps; ++b) {
           if (b < b0 || b >= b1) continue;
-          FixedSplit::add(&rhi[rowoff + b], &rlo[rowoff + b], wc[b] * va, two_k);
-          FixedSplit::add(&ihi[rowoff + b], &ilo[rowoff + b], wc[b] * vb, two_k);
+          const bool first = b < bsplit;
+          atomicAdd(&are[rowoff + b], __float2int_rn(wc[b] * (first ? va0 : va1)));
+          atomicAdd(&aim[rowoff + b], __float2int_rn(wc[b] * (first ? vb0 : vb1)));
         }
       }
     }
   }
   __syncthreads();
   float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
-  // value = ((hi << ksh) + lo) 2^-(e + ksh): exact in int64, one rounding to float,
-  // then two power-of-two scalings (exact unless the result is subnormal)
-  const float inv_e = __uint_as_float((unsigned)(127 - e) << 23);
-  const float inv_k = __uint_as_float((unsigned)(127 - ksh) << 23);
   for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
     const int rr = q / T, cc = q % T, o = rr * TP + cc;
-    const long long vr = ((long long)rhi[o] << ksh) + rlo[o];
-    const long long vi = ((long long)ihi[o] << ksh) + ilo[o];
+    const float inv = 1.f / sbS[(rr / kGridSB) * NSB + cc / kGridSB];    // power of two: exact
     const int row = phys_row2(tr * T + rr, vg);
-    gl[(size_t)row * vg.K2 + tc * T + cc] =
-        make_float2((float)vr * inv_k * inv_e, (float)vi * inv_k * inv_e);
+    gl[(size_t)row * vg.K2 + tc * T + cc] = make_float2((float)are[o] * inv, (float)aim[o] * inv);
   }
 }
 
@@ -970,7 +990,7 @@ void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, flo
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
-  size_t sm = 4 * (size_t)cb.tile * (cb.tile + 1) * sizeof(int);
+  size_t sm = 2 * (size_t)cb.tile * (cb.tile + 1) * sizeof(int);
   k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
                                vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);

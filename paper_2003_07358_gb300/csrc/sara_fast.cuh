@@ -177,17 +177,23 @@ __device__ __forceinline__ void syn2_stage(const Syn2& s, int l, int r0, int c0,
   const int kc = threadIdx.x & 31, kr0 = threadIdx.x >> 5;   // lane = column, warp = row (step 8)
   if (kc < KN) {
     const int klo = r0 / 2, gc = c0 / 2 + kc;
-    const bool vc = gc < s.mo2;
+    // rows kr0, kr0 + 8, ... of this thread that lie inside the band (none if the column is out)
+    const int nrows = gc < s.mo2 ? min((KN - kr0 + 7) / 8, max(0, (s.mo1 - klo - kr0 + 7) / 8)) : 0;
     const float* Wl = s.W + (size_t)l * s.I;
     const float* b0 = s.ll ? s.ll + (size_t)l * s.mo1 * s.mo2 : Wl + s.off[3];
-    const float* bp[4] = {b0, Wl + s.off[0], Wl + s.off[1], Wl + s.off[2]};
+    const int64_t start = (int64_t)(klo + kr0) * s.mo2 + gc, step = 8 * (int64_t)s.mo2;
+    const float* bp[4] = {b0 + start, Wl + s.off[0] + start, Wl + s.off[1] + start, Wl + s.off[2] + start};
+    float* dst = tc + kr0 * (kKn2 + 1) + kc;
 #pragma unroll
     for (int band = 0; band < 4; ++band) {
+      const float* src = bp[band];
 #pragma unroll
-      for (int kr = kr0; kr < KN; kr += 8) {
-        const int gk = klo + kr;
-        const bool v = vc && gk < s.mo1;
-        cp_async4(&tc[band * kTS2 + kr * (kKn2 + 1) + kc], bp[band] + (v ? (int64_t)gk * s.mo2 + gc : 0), v);
+      for (int j = 0; j < (KN + 7) / 8; ++j) {
+        if (kr0 + 8 * j < KN) {
+          const bool v = j < nrows;
+          cp_async4(dst + band * kTS2 + 8 * j * (kKn2 + 1), v ? src : b0, v);
+        }
+        src += step;
       }
     }
   }
@@ -315,25 +321,24 @@ struct SynFin2 {
 
 // Level 1 of all bases: the tiles of basis b + 1 are staged (cp.async) while basis b
 // is computed.
-__global__ void __launch_bounds__(256, 4) k_synfin(SynFin2 s, float* __restrict__ A) {
+__global__ void __launch_bounds__(256, 3) k_synfin(SynFin2 s, float* __restrict__ A) {
   __shared__ float sh[2 * 4 * kTS2 + 2 * kT2 * (kKn2 + 1)];
-  float* tcb[2] = {sh, sh + 4 * kTS2};
   float* lx = sh + 8 * kTS2;
   float* hx = lx + kT2 * (kKn2 + 1);
   const int l = blockIdx.z;
   const int r0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  syn2_stage_any(0, s.lv[0], l, r0, c0, tcb[0]);
+  syn2_stage_any(0, s.lv[0], l, r0, c0, sh);
 #pragma unroll 1
   for (int b = 0; b < 8; ++b) {
     if (b + 1 < 8) {
-      syn2_stage_any(b + 1, s.lv[b + 1], l, r0, c0, tcb[(b + 1) & 1]);
+      syn2_stage_any(b + 1, s.lv[b + 1], l, r0, c0, sh + ((b + 1) & 1) * 4 * kTS2);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    syn2_compute_any(b, tcb[b & 1], lx, hx, 1.f, acc);
+    syn2_compute_any(b, sh + (b & 1) * 4 * kTS2, lx, hx, 1.f, acc);
   }
   const int il = threadIdx.x >> 3, jc0 = 4 * (threadIdx.x & 7);
   const int r = r0 + il;
