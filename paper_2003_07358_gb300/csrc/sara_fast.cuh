@@ -25,19 +25,16 @@ constexpr int kT2 = 32;                              // tile side (coefficients 
 constexpr int kIn2 = 2 * kT2 + kMaxFilt - 2;         // 78: input rows/cols of an analysis tile
 constexpr int kKn2 = kT2 / 2 + kMaxFilt / 2;         // 24: coefficient rows/cols of a synthesis tile
 
-// Filter taps of basis F/2 - 1.  With compile-time indices the FMAs take them as
-// constant-bank operands, so they occupy no registers.
+// Filter taps of basis F/2 - 1, read straight from the constant bank: with the tap
+// index known at compile time (unrolled loops) every FMA takes the tap as a
+// constant-bank operand, no register and no load.
 template <int F>
 struct FTaps {
-  struct Row {
-    const float* p;
-    __device__ __forceinline__ float operator[](int t) const { return p[t]; }
-  };
-  Row h, g;
-  __device__ __forceinline__ void load() {
-    h.p = c_filt.h[F / 2 - 1];
-    g.p = c_filt.g[F / 2 - 1];
-  }
+  struct H { __device__ __forceinline__ float operator[](int t) const { return c_filt.h[F / 2 - 1][t]; } };
+  struct G { __device__ __forceinline__ float operator[](int t) const { return c_filt.g[F / 2 - 1][t]; } };
+  H h;
+  G g;
+  __device__ __forceinline__ void load() {}
 };
 
 // ------------------------------------------------------------- analysis
