@@ -394,10 +394,12 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
   std::vector<float2> uv_int(cb.n_vis);
   std::vector<uint8_t> blk_int(cb.n_vis);
   std::vector<int32_t> key, cnt(nkeys + 1);
-  std::vector<uint8_t> blk_user;
+  std::vector<uint8_t> blk_user, res;
+  std::vector<int64_t> order, slots;
   for (int l = 0; l < d.L; ++l) {
     const int64_t off = cb.vis_off[l], m = cb.vis_off[l + 1] - off;
     key.assign(m, 0);
+    res.assign(m, 0);
     blk_user.assign(m, 0);
     {
       int64_t k = 0;
@@ -415,13 +417,38 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
       bool down = lr + kTaps - 1 >= T, right = lc + kTaps - 1 >= T;
       int cls = down ? (right ? 2 : 1) : (right ? 3 : 0);
       key[i] = (tr * cb.ntile_c + tc) * 4 + cls;
+      res[i] = (uint8_t)((lr + lc) & 31);
       cnt[key[i] + 1]++;
     }
     for (int k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
     int32_t* to = &tile_off[(size_t)l * (nkeys + 1)];
     for (int k = 0; k <= nkeys; ++k) to[k] = cnt[k];
-    for (int64_t i = 0; i < m; ++i) {
-      int64_t pos = off + cnt[key[i]]++;
+    order.assign(m, 0);
+    for (int64_t i = 0; i < m; ++i) order[cnt[key[i]]++] = i;
+    // Within each (tile, class) bucket, deal the visibilities round-robin over the
+    // residue (lr + lc) mod 32 of their first tap: 32 consecutive visibilities then
+    // have distinct residues, so the 32 lanes of a warp touch 32 different shared-
+    // memory banks at every tap in the gridder and 16 different bank pairs in the
+    // tile-staged degridder (row strides = 1 mod 32 and 1 mod 16 cells).
+    for (int k = 0; k < nkeys; ++k) {
+      const int64_t b0 = to[k], b1 = to[k + 1];
+      if (b1 - b0 <= 1) continue;
+      int64_t rc[33] = {0};
+      for (int64_t j = b0; j < b1; ++j) rc[res[order[j]] + 1]++;
+      int64_t maxc = 0;
+      for (int r = 0; r < 32; ++r) maxc = std::max(maxc, rc[r + 1]);
+      for (int r = 0; r < 32; ++r) rc[r + 1] += rc[r];
+      slots.assign(b1 - b0, 0);
+      int64_t fill[32];
+      for (int r = 0; r < 32; ++r) fill[r] = rc[r];
+      for (int64_t j = b0; j < b1; ++j) slots[fill[res[order[j]]]++] = order[j];
+      int64_t o = b0;
+      for (int64_t rank = 0; rank < maxc; ++rank)
+        for (int r = 0; r < 32; ++r)
+          if (rc[r] + rank < rc[r + 1]) order[o++] = slots[rc[r] + rank];
+    }
+    for (int64_t j = 0; j < m; ++j) {
+      const int64_t i = order[j], pos = off + j;
       cb.perm_host[pos] = off + i;
       uv_int[pos] = make_float2(d.uv[2 * (off + i)], d.uv[2 * (off + i) + 1]);
       blk_int[pos] = blk_user[i];

@@ -585,7 +585,9 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
     for (int k = threadIdx.x; k < 8 * 2 * kMaxB; k += blockDim.x) (&sacc[0][0][0])[k] = 0.0;
   }
   const float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
-  const int R = T + kTaps - 1, SP = T + kTaps;      // staged side, odd row stride
+  // staged side R; row stride SP = 1 mod 16 (float2 units) so that bank pair = (row + col)
+  // mod 16, which the residue order of the visibilities spreads over the warp
+  const int R = T + kTaps - 1, SP = ((R + 14) / 16) * 16 + 1;
   const bool staged = end - beg >= kDegStageMin;
   if (staged) {
     for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
@@ -932,7 +934,8 @@ int degrid_parts(const Cube& cb) { return (int)((cb.max_M + 255) / 256); }
 int degrid_tiled_parts(const Cube& cb) { return cb.ntile_r * cb.ntile_c; }
 
 static size_t degrid_tiled_smem(const Cube& cb) {
-  return (size_t)(cb.tile + kTaps - 1) * (cb.tile + kTaps) * sizeof(float2);
+  const int R = cb.tile + kTaps - 1, SP = ((R + 14) / 16) * 16 + 1;
+  return (size_t)R * SP * sizeof(float2);
 }
 
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st) {
