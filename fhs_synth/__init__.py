@@ -86,6 +86,12 @@ WORKLOADS = {
                       n=4096, L=64, C=4, Q=16, overlap=0.1, m_ratio=0.5, B=8,
                       isnr_db=30.0, n_blobs=250, n_points=250, curvature=0.01,
                       seed=4000),
+    # the large workload's geometry (image, grid, facets, visibility density) on two
+    # channels of one sub-cube: a few GB on the device, for profiler captures
+    "large_slice": CubeSpec("large_slice: 4096x4096, L=2 (1 sub-cube), 16x16 facets, M=0.5N, B=8",
+                            n=4096, L=2, C=1, Q=16, overlap=0.1, m_ratio=0.5, B=8,
+                            isnr_db=30.0, n_blobs=250, n_points=250, curvature=0.01,
+                            seed=4000),
 }
 
 

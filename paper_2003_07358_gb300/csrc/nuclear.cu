@@ -42,7 +42,13 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
                                               const NucFacet* __restrict__ facets, const float* __restrict__ win,
                                               int n1, int n2, int L, int use_P, double* __restrict__ part,
                                               int nchunk_max) {
-  __shared__ float z[kGramSub][kMaxL + 1];
+  // the staged sub-chunk and, after the last one, the per-group partial sums
+  __shared__ union {
+    float z[kGramSub][kMaxL + 1];
+    double red[256 * LB * LB];
+  } sm;
+  auto& z = sm.z;
+  auto& red = sm.red;
   const int q = blockIdx.y;
   const NucFacet f = facets[q];
   const int h = f.r1 - f.r0, w = f.c1 - f.c0;
@@ -52,8 +58,15 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
   const int p1 = min(Nq, p0 + kGramChunk);
   const int Lp = (L + LB - 1) / LB * LB;
   const int nb = Lp / LB;
-  const int ta = threadIdx.x / nb, tb = threadIdx.x % nb;
-  const bool active = ta < nb && ta <= tb;
+  // thread -> (upper-triangle block pair, pixel group): npairs pairs, G groups share
+  // the pixels of each staged sub-chunk; the groups are summed in a fixed order
+  const int npairs = nb * (nb + 1) / 2;
+  const int G = max(1, (int)blockDim.x / npairs);
+  const int pair = threadIdx.x % npairs, g = threadIdx.x / npairs;
+  const bool active = g < G;
+  int ta = 0, rem = pair;
+  while (rem >= nb - ta) { rem -= nb - ta; ++ta; }
+  const int tb = ta + rem;
   float hi[LB][LB], lo[LB][LB];
 #pragma unroll
   for (int i = 0; i < LB; ++i)
@@ -66,7 +79,7 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
       int p = s0 + pix;
       float val = 0.f;
       if (p < p1 && l < L) {
-        int rr = p / w, cc = p % w;
+        int rr = p / w, cc = p - rr * w;
         float d = facet_weight(f, win, rr, cc);
         val = d * xc[l * N + (size_t)(f.r0 + rr) * n2 + (f.c0 + cc)];
         if (use_P) val += P[f.p_off + (size_t)l * Nq + p];
@@ -75,7 +88,7 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
     }
     __syncthreads();
     if (active) {
-      for (int pix = 0; pix < kGramSub; ++pix) {
+      for (int pix = g; pix < kGramSub; pix += G) {
         float a[LB], b[LB];
 #pragma unroll
         for (int i = 0; i < LB; ++i) a[i] = z[pix][ta * LB + i];
@@ -97,18 +110,24 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
     __syncthreads();
   }
   if (active) {
-    double* out = part + ((size_t)q * nchunk_max + blockIdx.x) * L * L;
 #pragma unroll
     for (int i = 0; i < LB; ++i)
 #pragma unroll
-      for (int j = 0; j < LB; ++j) {
-        int a = ta * LB + i, b = tb * LB + j;
-        double v = (double)hi[i][j] + (double)lo[i][j];
-        if (a < L && b < L) {
-          out[a * L + b] = v;
-          out[b * L + a] = v;
-        }
-      }
+      for (int j = 0; j < LB; ++j) red[((size_t)g * npairs + pair) * LB * LB + i * LB + j] = (double)hi[i][j] + (double)lo[i][j];
+  }
+  __syncthreads();
+  double* out = part + ((size_t)q * nchunk_max + blockIdx.x) * L * L;
+  for (int k = threadIdx.x; k < npairs * LB * LB; k += blockDim.x) {
+    const int pr = k / (LB * LB), ij = k - pr * LB * LB, i = ij / LB, j = ij - i * LB;
+    double v = 0.0;
+    for (int gg = 0; gg < G; ++gg) v += red[((size_t)gg * npairs + pr) * LB * LB + ij];
+    int xa = 0, xr = pr;
+    while (xr >= nb - xa) { xr -= nb - xa; ++xa; }
+    const int a = xa * LB + i, b = (xa + xr) * LB + j;
+    if (a < L && b < L) {
+      out[a * L + b] = v;
+      out[b * L + a] = v;
+    }
   }
 }
 
@@ -349,8 +368,8 @@ void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P,
   int use_P = (P != nullptr && !weights_mode) ? 1 : 0;
   if (weights_mode)
     k_gram_f64<<<gg, 256, 0, st>>>(xcheck, cb.d_facets, cb.d_win64, cb.n1, cb.n2, L, ctx->s.gram, nch);
-  else if (L <= 16) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
-  else if (L <= 32) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  else if (L <= 4) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  else if (L <= 16) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   else k_gram<4><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   note_launches(1);
   size_t sm = (size_t)2 * L * (L + 1) * sizeof(double) + L * sizeof(double) + L * sizeof(int);

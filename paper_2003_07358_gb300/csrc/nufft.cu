@@ -878,33 +878,39 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
       }
       if (pass == 0 && v_write) v_write[i] = val;
       float wc[kTaps], xr;
-      int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
-      int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
+      const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
+      const int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
       // footprint start in the source tile, then the taps of quadrant (dr, dc)
       // relative to this tile: rows lr + a - dr T, a in [a0, a1)
       const int lr = (kr & (vg.K1 - 1)) - sr * T - dr * T;
       const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
       const int a0 = max(0, -lr), a1 = min(kTaps, T - lr);
       const int b0 = max(0, -lc), b1 = min(kTaps, T - lc);
-      // the footprint spans at most two sub-block columns: b < bsplit -> first
-      const int c0 = min(max(lc, 0) / kGridSB, NSB - 1);
-      const int bsplit = (c0 + 1) * kGridSB - lc;
+      // the footprint spans at most two sub-blocks per axis: a < asplit (b < bsplit)
+      // takes the first; the four scales are read once per visibility
+      const int r0 = min(max(lr, 0) / kGridSB, NSB - 1), c0 = min(max(lc, 0) / kGridSB, NSB - 1);
+      const int r1 = min(r0 + 1, NSB - 1), c1 = min(c0 + 1, NSB - 1);
+      const int asplit = (r0 + 1) * kGridSB - lr, bsplit = (c0 + 1) * kGridSB - lc;
+      const float S00 = sbS[r0 * NSB + c0], S01 = sbS[r0 * NSB + c1];
+      const float S10 = sbS[r1 * NSB + c0], S11 = sbS[r1 * NSB + c1];
+      // rolled row loop over all 7 rows (a warp-uniform, so the row weight's constant-
+      // bank coefficients are broadcast); rows outside [a0, a1) are skipped
 #pragma unroll 1
       for (int a = 0; a < kTaps; ++a) {
         if (a < a0 || a >= a1) continue;
+        const bool top = a < asplit;
+        const float Sa = top ? S00 : S10, Sb = top ? S01 : S11;
         const float wa = kb_tap(a, xr);
-        const int rr = lr + a;
-        const int rowoff = rr * TP + lc;
-        const int sbr = (rr / kGridSB) * NSB;
-        const float S0 = sbS[sbr + c0], S1 = sbS[sbr + min(c0 + 1, NSB - 1)];
-        const float va0 = wa * val.x * S0, vb0 = wa * val.y * S0;
-        const float va1 = wa * val.x * S1, vb1 = wa * val.y * S1;
+        const float va0 = wa * val.x * Sa, vb0 = wa * val.y * Sa;
+        const float va1 = wa * val.x * Sb, vb1 = wa * val.y * Sb;
+        int* pr = are + (lr + a) * TP + lc;
+        int* pi = aim + (lr + a) * TP + lc;
 #pragma unroll
         for (int b = 0; b < kTaps; ++b) {
           if (b < b0 || b >= b1) continue;
           const bool first = b < bsplit;
-          atomicAdd(&are[rowoff + b], __float2int_rn(wc[b] * (first ? va0 : va1)));
-          atomicAdd(&aim[rowoff + b], __float2int_rn(wc[b] * (first ? vb0 : vb1)));
+          atomicAdd(pr + b, __float2int_rn(wc[b] * (first ? va0 : va1)));
+          atomicAdd(pi + b, __float2int_rn(wc[b] * (first ? vb0 : vb1)));
         }
       }
     }
