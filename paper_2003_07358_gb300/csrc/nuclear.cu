@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
     for (int j = 0; j < LB; ++j) hi[i][j] = lo[i][j] = 0.f;
   const size_t N = (size_t)n1 * n2;
   for (int s0 = p0; s0 < p1; s0 += kGramSub) {
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < kGramSub * Lp; idx += blockDim.x) {
       int pix = idx % kGramSub, l = idx / kGramSub;
       int p = s0 + pix;
@@ -203,7 +204,11 @@ __global__ void __launch_bounds__(32) k_eig(const double* __restrict__ part, int
   double* G = sh;                 // [L][L+1]
   double* V = sh + L * Ls;        // [L][L+1]
   double* lam = V + L * Ls;       // [L]
-  int* rank = (int*)(lam + L);    // [L]
+  double* rc = lam + L;           // [L/2 + 1] rotation cosines of a round
+  double* rs = rc + (L / 2 + 1);  // [L/2 + 1] sines
+  int* rank = (int*)(rs + (L / 2 + 1));   // [L]
+  int* rp = rank + L;             // [L/2 + 1] pair indices
+  int* rr = rp + (L / 2 + 1);
   const int q = blockIdx.x, lane = threadIdx.x;
   const NucFacet f = facets[q];
   const int Nq = (f.r1 - f.r0) * (f.c1 - f.c0);
@@ -227,6 +232,7 @@ __global__ void __launch_bounds__(32) k_eig(const double* __restrict__ part, int
   }
   __syncwarp();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    __syncwarp();
     double off = 0.0, dia = 0.0;
     for (int idx = lane; idx < L * L; idx += 32) {
       int a = idx / L, b = idx % L;
@@ -239,33 +245,55 @@ __global__ void __launch_bounds__(32) k_eig(const double* __restrict__ part, int
       dia += __shfl_xor_sync(0xffffffffu, dia, o);
     }
     if (off <= 1e-30 * dia || off == 0.0) break;
-    for (int p = 0; p < L - 1; ++p) {
-      for (int r = p + 1; r < L; ++r) {
-        double gpr = G[p * Ls + r];
-        double gpp = G[p * Ls + p], grr = G[r * Ls + r];
-        if (fabs(gpr) <= 1e-300 || fabs(gpr) <= 1e-18 * sqrt(fabs(gpp * grr))) continue;
-        double th = (grr - gpp) / (2.0 * gpr);
-        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-        double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-        __syncwarp();
-        for (int k = lane; k < L; k += 32) {     // rows p, r
-          double a = G[p * Ls + k], b = G[r * Ls + k];
-          G[p * Ls + k] = c * a - s * b;
-          G[r * Ls + k] = s * a + c * b;
+    // one sweep = Le - 1 rounds of the round-robin tournament over Le = L rounded up to
+    // even (index L is a dummy); a round rotates Le/2 disjoint pairs at once: lane j
+    // computes pair j's rotation from the round's G, then rows and columns are
+    // updated for all pairs (the pairs are disjoint, so this is exact)
+    const int Le = (L + 1) & ~1, H = Le / 2;
+    for (int rnd = 0; rnd < Le - 1; ++rnd) {
+      auto player = [&](int k) { return k == 0 ? 0 : ((k - 1 + rnd) % (Le - 1)) + 1; };
+      __syncwarp();
+      for (int j = lane; j < H; j += 32) {
+        int p = player(j), r = player(Le - 1 - j);
+        if (p > r) { int t = p; p = r; r = t; }
+        double c = 1.0, sn = 0.0;
+        if (r < L) {
+          const double gpr = G[p * Ls + r], gpp = G[p * Ls + p], grr = G[r * Ls + r];
+          if (fabs(gpr) > 1e-300 && fabs(gpr) > 1e-18 * sqrt(fabs(gpp * grr))) {
+            const double th = (grr - gpp) / (2.0 * gpr);
+            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
         }
-        __syncwarp();
-        for (int k = lane; k < L; k += 32) {     // columns p, r and eigenvectors
-          double a = G[k * Ls + p], b = G[k * Ls + r];
-          G[k * Ls + p] = c * a - s * b;
-          G[k * Ls + r] = s * a + c * b;
-          double va = V[k * Ls + p], vb = V[k * Ls + r];
-          V[k * Ls + p] = c * va - s * vb;
-          V[k * Ls + r] = s * va + c * vb;
-        }
-        __syncwarp();
+        rp[j] = p; rr[j] = r; rc[j] = c; rs[j] = sn;
+      }
+      __syncwarp();
+      for (int idx = lane; idx < H * L; idx += 32) {     // rows p, r
+        const int j = idx / L, k = idx - j * L;
+        const int p = rp[j], r = rr[j];
+        if (r >= L || rs[j] == 0.0) continue;
+        const double c = rc[j], sn = rs[j];
+        const double a = G[p * Ls + k], b = G[r * Ls + k];
+        G[p * Ls + k] = c * a - sn * b;
+        G[r * Ls + k] = sn * a + c * b;
+      }
+      __syncwarp();
+      for (int idx = lane; idx < H * L; idx += 32) {     // columns p, r and eigenvectors
+        const int j = idx / L, k = idx - j * L;
+        const int p = rp[j], r = rr[j];
+        if (r >= L || rs[j] == 0.0) continue;
+        const double c = rc[j], sn = rs[j];
+        const double a = G[k * Ls + p], b = G[k * Ls + r];
+        G[k * Ls + p] = c * a - sn * b;
+        G[k * Ls + r] = sn * a + c * b;
+        const double va = V[k * Ls + p], vb = V[k * Ls + r];
+        V[k * Ls + p] = c * va - sn * vb;
+        V[k * Ls + r] = sn * va + c * vb;
       }
     }
   }
+  __syncwarp();
   for (int j = lane; j < L; j += 32) lam[j] = G[j * Ls + j];
   __syncwarp();
   for (int j = lane; j < L; j += 32) {
@@ -372,7 +400,8 @@ void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P,
   else if (L <= 16) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   else k_gram<4><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   note_launches(1);
-  size_t sm = (size_t)2 * L * (L + 1) * sizeof(double) + L * sizeof(double) + L * sizeof(int);
+  size_t sm = (size_t)2 * L * (L + 1) * sizeof(double) + L * sizeof(double) + 2 * (L / 2 + 1) * sizeof(double) +
+              (L + 2 * (L / 2 + 1)) * sizeof(int);
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024); attr = true; }
   k_eig<<<Q, 32, sm, st>>>(ctx->s.gram, nch, cb.d_facets, L, theta_bar, cb.d_mubar, (float)(1.0 / cb.zeta),

@@ -590,11 +590,22 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
   const int R = T + kTaps - 1, SP = ((R + 14) / 16) * 16 + 1;
   const bool staged = end - beg >= kDegStageMin;
   if (staged) {
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-      const int rr = idx / R, cc = idx - rr * R;
-      const int row = phys_row2((tr * T + rr) & (vg.K1 - 1), vg);
-      sg[rr * SP + cc] = gl[(size_t)row * vg.K2 + ((tc * T + cc) & (vg.K2 - 1))];
+    // asynchronous 8-byte copies (all of a thread's loads in flight): lane = column,
+    // warp = row
+    const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < R; c0 += 32) {
+      const int cc = c0 + lane;
+      if (cc >= R) continue;
+      const int col = (tc * T + cc) & (vg.K2 - 1);
+#pragma unroll 4
+      for (int rr = wrp; rr < R; rr += 8) {
+        const int row = phys_row2((tr * T + rr) & (vg.K1 - 1), vg);
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(&sg[rr * SP + cc]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gl + (size_t)row * vg.K2 + col));
+      }
     }
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::);
   }
   __syncthreads();
   for (int base = beg; base < end; base += blockDim.x) {

@@ -37,6 +37,16 @@ struct FTaps {
   __device__ __forceinline__ void load() {}
 };
 
+// ------------------------------------------------------------- async copies
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 // ------------------------------------------------------------- analysis
 template <int F>
 __global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, float* __restrict__ ll_out,
@@ -53,10 +63,24 @@ __global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, floa
   const int k0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
   const int r_in0 = 2 * k0 + 2 - F, c_in0 = 2 * c0 + 2 - F;
   const float* inl = in + (size_t)l * m1 * m2;
-  for (int idx = threadIdx.x; idx < IN * IN; idx += 256) {
-    int r = idx / IN, c = idx - r * IN;
-    int gr = r_in0 + r, gc = c_in0 + c;
-    tin[r][c] = (gr >= 0 && gr < m1 && gc >= 0 && gc < m2) ? inl[(size_t)gr * m2 + gc] : 0.f;
+  // stage the input tile with asynchronous copies (zero fill outside the image), so
+  // that all of a thread's loads are in flight at once: lane = column, warp = row
+  {
+    const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
+#pragma unroll
+    for (int cj = 0; cj < (IN + 31) / 32; ++cj) {
+      const int c = lane + 32 * cj, gc = c_in0 + c;
+      if (c >= IN) continue;
+      const bool vc = gc >= 0 && gc < m2;
+#pragma unroll 4
+      for (int r = wrp; r < IN; r += 8) {
+        const int gr = r_in0 + r;
+        const bool v = vc && gr >= 0 && gr < m1;
+        cp_async4(&tin[r][c], v ? inl + (size_t)gr * m2 + gc : inl, v);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
   }
   __syncthreads();
   // x: lx[r][kc] = sum_t h[t] tin[r][2 kc + F - 1 - t], 4 consecutive kc per item
@@ -153,15 +177,6 @@ struct Syn2 {
   int64_t off[4];      // d0, d1, d2, LL4
   int mo1, mo2, m1, m2;
 };
-
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  int n = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 constexpr int kTS2 = kKn2 * (kKn2 + 1);             // one staged band
 
