@@ -195,6 +195,31 @@ def op_bytes(spec: fs.CubeSpec, n_coef: int, n_facet_pix: int) -> dict:
     }
 
 
+def grid_launch_bytes(spec: fs.CubeSpec) -> int:
+    """Algorithmic bytes of one gridding launch (one sub-cube): the 2n x 2n complex64
+    grid of each channel written once, and per visibility uv (8 B), value (8 B), block
+    id (1 B) read and the scaled dual v (8 B) written."""
+    K2 = (2 * spec.n) ** 2
+    return spec.Lc * (8 * K2 + 25 * spec.M)
+
+
+def grid_traffic(spec: fs.CubeSpec):
+    """DRAM bytes (read + write) of one gridding launch from the committed ncu
+    summary of the large_slice capture, scaled by channels per launch; None when the
+    summary is absent or was taken on another workload geometry."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "k_grid_large_slice_ncu.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("dram_bytes_per_channel ="):
+                    per_ch = float(line.split("=")[1].split()[0])
+                    if spec.n == 4096 and spec.M == fs.workload("large_slice").M:
+                        return int(per_ch * spec.Lc)
+    except OSError:
+        pass
+    return None
+
+
 # ------------------------------------------------------------- CPU oracle
 def oracle_iteration_estimate(spec: fs.CubeSpec, budget_scale: float = 1.0) -> dict:
     """Seconds of one oracle iteration of the workload, from timed samples of
@@ -304,6 +329,9 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    # CUDA events around the gridding kernel inside the captured iteration (the
+    # dominant kernel of the iteration), read after the timed region
+    ctx.fhs_set_kernel_timer("grid")
     for _ in range(args.warmup):
         ctx.fhs_pdfb_iter(its, 1, want_stats=False)
     st = ctx.fhs_pdfb_iter(its, 1, want_stats=True)
@@ -322,6 +350,8 @@ def main():
     barrier()
     launches = ctx.fhs_kernel_launches() - l0
     clocks = sampler.stop()
+    grid_ms, grid_n = ctx.fhs_kernel_timer_read()
+    ctx.fhs_set_kernel_timer(None)
     ms = sh.max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, device="cuda")
     value = sh.weak_scaling_value(1, world, ms / 1000.0)
     log(f"{ms:.1f} ms per iteration")
@@ -377,13 +407,16 @@ def main():
                       "GB_s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 4)}
         ops["primal"] = {"algorithmic_GB": round(byts["primal"] / 1e9, 3)}
         del A, ybuf
-    dominant = max((k for k in ops if "ms_per_subcube" in ops[k]), key=lambda k: ops[k]["ms_per_subcube"],
-                   default=None)
-    roofline = None
-    if dominant:
-        d = ops[dominant]
-        roofline = {"bound": "hbm", "kernel": dominant, "achieved": d["GB_s"], "peak": hbm, "unit": "GB/s",
-                    "frac": d["frac_of_hbm"], "traffic": None, "peak_kind": peak_kind}
+    # roofline of the dominant kernel, the gridder G^T: one launch grids one sub-cube,
+    # algorithmic bytes = grid written once (L K1 K2 8 B) + per visibility uv, value,
+    # block id read and v written (25 B); time = its CUDA events in the last timed iteration
+    g_bytes = grid_launch_bytes(spec)
+    g_s = grid_ms / grid_n / 1000.0
+    g_ach = g_bytes / g_s / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_grid (gridding G^T, one sub-cube per launch)",
+                "achieved": round(g_ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(g_ach / hbm, 4),
+                "traffic": grid_traffic(spec), "peak_kind": peak_kind,
+                "ms_per_launch": round(g_s * 1e3, 3), "algorithmic_GB_per_launch": round(g_bytes / 1e9, 3)}
 
     # end to end through the C ABI with host buffers: H2D of y, one iteration, D2H of the statistics
     e2e = None

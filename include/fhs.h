@@ -207,6 +207,20 @@ fhs_status fhs_set_path(fhs_ctx* ctx, int32_t path);
 /* Number of CUDA kernels this library has launched in this process so far. */
 uint64_t fhs_kernel_launches(void);
 
+/* Kernel timer (a measurement hook; the paper has no counterpart).  With
+ * kernel = FHS_TIMER_GRID (the gridding kernel, G^T of Algorithm 2) or
+ * FHS_TIMER_DEGRID (the degridding + l2-ball data-dual kernel), fhs_pdfb_iter
+ * records a CUDA event pair around that kernel's launch for every cube, inside
+ * its CUDA graph as well; FHS_TIMER_NONE (default) records nothing.  Changing
+ * the selection re-captures the graph on the next call.
+ * fhs_kernel_timer_read synchronises on the last recorded events and returns
+ * the summed device time (ms) of the selected kernel's launches in the most
+ * recent iteration and their number (the cube count); FHS_ERR_INVALID_ARG if no
+ * timer is selected or no iteration has run since the selection. */
+enum { FHS_TIMER_NONE = 0, FHS_TIMER_GRID = 1, FHS_TIMER_DEGRID = 2 };
+fhs_status fhs_set_kernel_timer(fhs_ctx* ctx, int32_t kernel);
+fhs_status fhs_kernel_timer_read(fhs_ctx* ctx, double* ms_total, int32_t* launches);
+
 /* n_iter iterations of Algorithm 2 on every cube.  it: host [ncubes].
  * stats: host [ncubes] or NULL; when not NULL the call synchronises and
  * fills the statistics of the last iteration. */

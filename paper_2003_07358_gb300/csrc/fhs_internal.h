@@ -113,6 +113,11 @@ struct fhs_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<const void*> graph_key;
   uint64_t graph_kernels = 0;
+  // kernel timer: FHS_TIMER_* selection, one event pair per cube, whether an
+  // iteration has recorded them since the selection
+  int timer = FHS_TIMER_NONE;
+  std::vector<cudaEvent_t> tev;
+  bool timer_armed = false;
 };
 
 namespace fhs {

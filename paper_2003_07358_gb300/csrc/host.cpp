@@ -594,6 +594,12 @@ void adjoint_into(fhs_ctx* ctx, const Cube& cb, const float2* vals, const float*
   check_launch("adjoint");
 }
 
+// Event k of the kernel timer when `which` is the selected kernel.
+void timer_mark(fhs_ctx* ctx, int which, int k) {
+  if (ctx->timer != which) return;
+  FHS_CUDA(cudaEventRecord(ctx->tev[k], ctx->stream));
+}
+
 // One iteration of Algorithm 2 on every cube, on ctx->stream; the primal partial
 // sums and the block norms of cube c land in its statistics region.
 void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
@@ -615,15 +621,21 @@ void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
     int np;
     if (use_fast(ctx, cb)) {
       np = degrid_tiled_parts(cb);
+      timer_mark(ctx, FHS_TIMER_DEGRID, 2 * c);
       launch_degrid_pdfb_tiled(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
                                (float2*)a.state.u_prev, ctx->s.red, st);
+      timer_mark(ctx, FHS_TIMER_DEGRID, 2 * c + 1);
     } else {
       np = degrid_parts(cb);
       launch_degrid_pdfb(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
                          (float2*)a.state.u_prev, ctx->s.red, np, st);
     }
     launch_block_finalize(cb, ctx->s.red, np, ctx->s.blk_scale, stat + 2 * pp, st);
-    adjoint_into(ctx, cb, ctx->s.vis, ctx->s.blk_scale, (float2*)a.state.v, A, cb.d_eta, true);
+    timer_mark(ctx, FHS_TIMER_GRID, 2 * c);
+    launch_grid(cb, ctx->s.vis, ctx->s.blk_scale, (float2*)a.state.v, ctx->s.grid, st);
+    timer_mark(ctx, FHS_TIMER_GRID, 2 * c + 1);
+    launch_fft_adjoint(ctx, cb, ctx->s.grid, A, cb.d_eta, true, st);
+    check_launch("adjoint");
     launch_primal(cb, a.X, a.Xcheck, A, stat, pp, st);
     check_launch("primal");
   }
@@ -690,6 +702,7 @@ fhs_status fhs_destroy(fhs_ctx* ctx) {
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   for (Cube& cb : ctx->cubes) free_cube(cb);
   free_scratch(ctx->s);
   if (ctx->d_tw) cudaFree(ctx->d_tw);
@@ -919,6 +932,39 @@ fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, d
 
 uint64_t fhs_kernel_launches(void) { return g_launches.load(); }
 
+fhs_status fhs_set_kernel_timer(fhs_ctx* ctx, int32_t kernel) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(kernel == FHS_TIMER_NONE || kernel == FHS_TIMER_GRID || kernel == FHS_TIMER_DEGRID,
+                FHS_ERR_INVALID_ARG, "unknown kernel timer");
+    const size_t need = 2 * ctx->cubes.size();
+    while (ctx->tev.size() < need) {
+      cudaEvent_t e;
+      FHS_CUDA(cudaEventCreate(&e));
+      ctx->tev.push_back(e);
+    }
+    ctx->timer = kernel;
+    ctx->timer_armed = false;
+  });
+}
+
+fhs_status fhs_kernel_timer_read(fhs_ctx* ctx, double* ms_total, int32_t* launches) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(ms_total && launches, FHS_ERR_INVALID_ARG, "NULL output");
+    FHS_REQUIRE(ctx->timer != FHS_TIMER_NONE && ctx->timer_armed, FHS_ERR_INVALID_ARG,
+                "no kernel timer selected, or no iteration since the selection");
+    const int nc = (int)ctx->cubes.size();
+    double tot = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      FHS_CUDA(cudaEventSynchronize(ctx->tev[2 * c + 1]));
+      float ms = 0.f;
+      FHS_CUDA(cudaEventElapsedTime(&ms, ctx->tev[2 * c], ctx->tev[2 * c + 1]));
+      tot += ms;
+    }
+    *ms_total = tot;
+    *launches = nc;
+  });
+}
+
 fhs_status fhs_set_path(fhs_ctx* ctx, int32_t path) {
   return guarded(ctx, [&] {
     FHS_REQUIRE(path == FHS_PATH_FAST || path == FHS_PATH_PLAIN, FHS_ERR_INVALID_ARG, "unknown path");
@@ -932,6 +978,7 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
     const int nc = (int)ctx->cubes.size();
     std::vector<const void*> key;
     key.push_back((const void*)(intptr_t)ctx->path);
+    key.push_back((const void*)(intptr_t)ctx->timer);
     for (int c = 0; c < nc; ++c) {
       const fhs_iterate& a = it[c];
       FHS_REQUIRE(a.X && a.Xcheck && a.y && a.state.W && a.state.theta && a.state.P && a.state.theta_bar &&
@@ -977,6 +1024,7 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
     }
     FHS_CUDA(cudaEventRecord(ctx->ev_out, ctx->gstream));
     FHS_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0));
+    if (ctx->timer != FHS_TIMER_NONE) ctx->timer_armed = true;
     if (!stats) return;
     std::vector<double> h(ctx->s.stat_stride * nc);
     FHS_CUDA(cudaMemcpyAsync(h.data(), ctx->s.stat, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

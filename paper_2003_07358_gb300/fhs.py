@@ -25,9 +25,11 @@ SYMBOLS = [
     "fhs_vis_to_internal", "fhs_vis_to_user", "fhs_measure", "fhs_adjoint", "fhs_opnorm_sq",
     "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_prox_l21_sara_facets", "fhs_prox_nuclear_facets",
     "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
-    "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path",
+    "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path", "fhs_set_kernel_timer",
+    "fhs_kernel_timer_read",
 ]
 FHS_PATH = {"fast": 0, "plain": 1}
+FHS_TIMER = {None: 0, "grid": 1, "degrid": 2}
 
 
 class FhsError(RuntimeError):
@@ -99,6 +101,8 @@ def load(path: str = LIB_PATH):
         "fhs_proj_l2ball_noalloc": ([vp, vp, i64p, i32, dp, vp, dp, vp], i32),
         "fhs_noalloc_last_error": ([], C.c_char_p),
         "fhs_set_path": ([vp, i32], i32),
+        "fhs_set_kernel_timer": ([vp, i32], i32),
+        "fhs_kernel_timer_read": ([vp, C.POINTER(C.c_double), C.POINTER(i32)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -287,6 +291,17 @@ class Context:
 
     def fhs_kernel_launches(self) -> int:
         return int(self.lib.fhs_kernel_launches())
+
+    def fhs_set_kernel_timer(self, kernel):
+        """Record CUDA events around one kernel of fhs_pdfb_iter: None, 'grid' or 'degrid'."""
+        self._check(self.lib.fhs_set_kernel_timer(self.h, FHS_TIMER[kernel]))
+
+    def fhs_kernel_timer_read(self):
+        """(summed ms, launches) of the timed kernel in the most recent iteration."""
+        ms = C.c_double()
+        n = C.c_int32()
+        self._check(self.lib.fhs_kernel_timer_read(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     # ------------------------------------------------------------ helpers
     def new_state(self, cube: int = 0) -> dict:
