@@ -595,9 +595,11 @@ void adjoint_into(fhs_ctx* ctx, const Cube& cb, const float2* vals, const float*
 }
 
 // Event k of the kernel timer when `which` is the selected kernel.
+// (External record: inside a stream capture it becomes an event-record node of the
+// graph, so every replay records the event.)
 void timer_mark(fhs_ctx* ctx, int which, int k) {
   if (ctx->timer != which) return;
-  FHS_CUDA(cudaEventRecord(ctx->tev[k], ctx->stream));
+  FHS_CUDA(cudaEventRecordWithFlags(ctx->tev[k], ctx->stream, cudaEventRecordExternal));
 }
 
 // One iteration of Algorithm 2 on every cube, on ctx->stream; the primal partial
