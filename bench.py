@@ -247,7 +247,7 @@ def oracle_iteration_estimate(spec: fs.CubeSpec, budget_scale: float = 1.0) -> d
     per_ch = 2 * t_fft + (t_deg + t_grd) * spec.M / ms
     out["data"] = per_ch * L
     # SARA: analysis + synthesis of a crop, scaled by area and channels
-    s = min(n, 512 if budget_scale >= 1 else 256)
+    s = min(n, 1024 if budget_scale >= 4 else (512 if budget_scale >= 1 else 256))
     xs = rng.random((1, s, s))
     t = time.perf_counter()
     cf = wv.sara_analysis(xs)
@@ -255,7 +255,7 @@ def oracle_iteration_estimate(spec: fs.CubeSpec, budget_scale: float = 1.0) -> d
     out["sara"] = (time.perf_counter() - t) * (n * n) / (s * s) * L
     # nuclear: Jacobi SVD of one facet-sized matrix, scaled by facets and sub-cubes
     side = n // Q + int(math.floor(spec.overlap * n / Q))
-    rows = min(side * side, 8192 if budget_scale >= 1 else 4096)
+    rows = min(side * side, 32768 if budget_scale >= 4 else (8192 if budget_scale >= 1 else 4096))
     Z = rng.standard_normal((rows, Lc))
     t = time.perf_counter()
     px.jacobi_svd(Z)
@@ -445,10 +445,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = time.time()
-        est = oracle_iteration_estimate(spec, 1.0)
+        est = oracle_iteration_estimate(spec, 4.0)
         cpu = {"value": 1.0 / est["total"], "unit": "iter/s", "cores": 1, "kind": "oracle",
-               "sample": ("one channel's 2n x 2n FFT, 20000 degrid + grid visibilities, SARA on a 512^2 crop, "
-                          "Jacobi SVD of an 8192 x 16 facet slice, one channel's primal update, each scaled "
+               "sample": ("one channel's 2n x 2n FFT, 80000 degrid + grid visibilities, SARA on a 1024^2 crop, "
+                          "Jacobi SVD of a 32768 x 16 facet slice, one channel's primal update, each scaled "
                           "to the units of one full iteration; seconds per iteration by operator: "
                           + ", ".join(f"{k} {v:.0f}" for k, v in est.items())),
                "wall_s": round(time.time() - t, 1)}
