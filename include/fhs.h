@@ -41,7 +41,7 @@ enum {
   FHS_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
   FHS_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed   */
   FHS_ERR_OOM = 3,         /* device memory for the context could not be allocated */
-  FHS_ERR_TIMEOUT = 4,     /* reserved: a bounded device-side wait gave up  */
+  FHS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (fhs_sync) */
   FHS_ERR_NONFINITE = 5,   /* a norm reduction produced NaN or Inf          */
   FHS_ERR_UNSUPPORTED = 6  /* shape outside what this build implements      */
 };

@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 Faceted HyperSARA library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,6 +73,11 @@ struct Cube {
   double* d_eps = nullptr;                   // [L*B]
   float* d_eta = nullptr;                    // [L]
   float* d_mubar = nullptr;                  // [Q]
+  // TMA descriptors of the degridder's tile staging over the context's grid scratch,
+  // viewed as [L][N1c][N2c][K2] (rows in the column transform's digit-reversed order):
+  // the T tile rows and the 6 halo rows of a grid tile
+  CUtensorMap tm_rows, tm_halo;
+  bool tma = false;
 };
 
 struct Scratch {
@@ -139,6 +145,8 @@ void launch_fft_forward_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float
 void launch_fft_adjoint_fast(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta,
                              bool accumulate, cudaStream_t st);
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st);
+void encode_degrid_maps(fhs_ctx* ctx);
+unsigned read_device_status(bool clear);
 int degrid_tiled_parts(const Cube& cb);
 void launch_degrid_pdfb_tiled(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
                               float2* u_prev, double* partials, cudaStream_t st);

@@ -417,7 +417,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
       bool down = lr + kTaps - 1 >= T, right = lc + kTaps - 1 >= T;
       int cls = down ? (right ? 2 : 1) : (right ? 3 : 0);
       key[i] = (tr * cb.ntile_c + tc) * 4 + cls;
-      res[i] = (uint8_t)((lr + lc) & 31);
+      res[i] = (uint8_t)(lc & 31);
       cnt[key[i] + 1]++;
     }
     for (int k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
@@ -426,10 +426,10 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
     order.assign(m, 0);
     for (int64_t i = 0; i < m; ++i) order[cnt[key[i]]++] = i;
     // Within each (tile, class) bucket, deal the visibilities round-robin over the
-    // residue (lr + lc) mod 32 of their first tap: 32 consecutive visibilities then
-    // have distinct residues, so the 32 lanes of a warp touch 32 different shared-
-    // memory banks at every tap in the gridder and 16 different bank pairs in the
-    // tile-staged degridder (row strides = 1 mod 32 and 1 mod 16 cells).
+    // column of their first tap mod 32: 32 consecutive visibilities then have distinct
+    // residues, so the 32 lanes of a warp touch 32 different shared-memory banks at
+    // every tap in the gridder and 16 different bank pairs in the tile-staged
+    // degridder (row strides multiples of 32 and 16 cells).
     for (int k = 0; k < nkeys; ++k) {
       const int64_t b0 = to[k], b1 = to[k + 1];
       if (b1 - b0 <= 1) continue;
@@ -680,6 +680,7 @@ fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, 
     ctx->d_tw = dalloc<float2>(kmax);
     upload(ctx->d_tw, tw.data(), tw.size(), ctx->stream);
     alloc_scratch(ctx);
+    encode_degrid_maps(ctx);
     FHS_CUDA(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
     FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
     FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
@@ -727,7 +728,10 @@ fhs_status fhs_get_sizes(const fhs_ctx* cctx, int32_t cube, fhs_sizes* out) {
 }
 
 fhs_status fhs_sync(fhs_ctx* ctx) {
-  return guarded(ctx, [&] { FHS_CUDA(cudaStreamSynchronize(ctx->stream)); });
+  return guarded(ctx, [&] {
+    FHS_CUDA(cudaStreamSynchronize(ctx->stream));
+    FHS_REQUIRE(read_device_status(true) == 0, FHS_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  });
 }
 
 const char* fhs_last_error(const fhs_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
@@ -1031,6 +1035,7 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
     std::vector<double> h(ctx->s.stat_stride * nc);
     FHS_CUDA(cudaMemcpyAsync(h.data(), ctx->s.stat, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     FHS_CUDA(cudaStreamSynchronize(ctx->stream));
+    FHS_REQUIRE(read_device_status(true) == 0, FHS_ERR_TIMEOUT, "a bounded device-side wait gave up");
     for (int c = 0; c < nc; ++c) {
       const Cube& cb = ctx->cubes[c];
       const double* st = h.data() + ctx->s.stat_stride * c;

@@ -21,6 +21,13 @@
 #include "fhs_internal.h"
 
 namespace fhs {
+// Device status word: bits set by bounded waits that gave up (read by the host).
+__device__ unsigned int g_dev_status = 0;
+}  // namespace fhs
+
+#include "tma.cuh"
+
+namespace fhs {
 
 __constant__ KbPoly c_kb;
 
@@ -559,11 +566,20 @@ __global__ void __launch_bounds__(256) k_degrid_pdfb(const float2* __restrict__ 
 // visibility of the tile has its first tap in the tile, so its 7 x 7 footprint lies
 // in the (T + 6)^2 region starting at the tile corner, which is staged in shared
 // memory once (coalesced rows) and then read by all of the tile's visibilities.
-// Tiles with few visibilities read the grid directly instead.  MODE 0 stores
+// Tiles with few visibilities read the grid directly instead.  The staging is two
+// TMA tensor copies (tile rows and halo rows of the digit-reversed grid, an mbarrier
+// with a bounded wait) except for the last tile column, whose halo wraps around the
+// grid edge and is staged with asynchronous 8-byte copies.  The staged row stride S
+// is a multiple of 16 float2 (the TMA box width), so a lane's bank pair is its column
+// mod 16, which the host's visibility order (first-tap column mod 32 distinct within
+// 32 consecutive visibilities) spreads over the warp.  MODE 0 stores
 // u = G x_hat; MODE 1 is the PDFB data step of k_degrid_pdfb with its per-block
 // partial sums accumulated per warp in shared memory over the tile (fixed order)
 // and written once per CTA: partials[l][tile][2][B].
 constexpr int kDegStageMin = 96;
+
+// Staged row stride of the degridder (float2): T + 6 rounded up to 16.
+__host__ __device__ inline int degrid_stage_stride(int T) { return ((T + kTaps - 1 + 15) / 16) * 16; }
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__ grid, const float2* __restrict__ uv,
@@ -572,9 +588,12 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
                                                       int ntr, int ntc, float2* __restrict__ out,
                                                       const float2* __restrict__ y, const float2* __restrict__ v,
                                                       float2* __restrict__ u_prev, const uint8_t* __restrict__ blk,
-                                                      int B, double* __restrict__ partials) {
-  extern __shared__ float2 sg[];
+                                                      int B, double* __restrict__ partials,
+                                                      const __grid_constant__ CUtensorMap tm_rows,
+                                                      const __grid_constant__ CUtensorMap tm_halo, int use_tma) {
+  extern __shared__ __align__(128) float2 sg[];
   __shared__ double sacc[8][2][kMaxB];
+  __shared__ __align__(8) uint64_t bar;
   const int l = blockIdx.y, tau = blockIdx.x;
   const int tr = tau / ntc, tc = tau % ntc;
   const int32_t* toff = tile_off + (size_t)l * (ntr * ntc * 4 + 1);
@@ -585,11 +604,20 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
     for (int k = threadIdx.x; k < 8 * 2 * kMaxB; k += blockDim.x) (&sacc[0][0][0])[k] = 0.0;
   }
   const float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
-  // staged side R; row stride SP = 1 mod 16 (float2 units) so that bank pair = (row + col)
-  // mod 16, which the residue order of the visibilities spreads over the warp
-  const int R = T + kTaps - 1, SP = ((R + 14) / 16) * 16 + 1;
+  const int R = T + kTaps - 1, SP = degrid_stage_stride(T);
   const bool staged = end - beg >= kDegStageMin;
-  if (staged) {
+  const bool tma = staged && use_tma && tc + 1 < ntc;
+  if (tma) {
+    if (threadIdx.x == 0) {
+      const int k0 = tr * T, k1 = (tr * T + T) & (vg.K1 - 1);
+      mbar_init(&bar, 1);
+      mbar_expect_tx(&bar, (unsigned)(R * SP * sizeof(float2)));
+      tma_load_4d(sg, &tm_rows, tc * T, k0 >> vg.lg1, k0 & (vg.N1c - 1), l, &bar);
+      tma_load_4d(sg + T * SP, &tm_halo, tc * T, k1 >> vg.lg1, k1 & (vg.N1c - 1), l, &bar);
+    }
+    __syncthreads();                       // the barrier is initialised before anyone waits
+    mbar_wait(&bar, 0);
+  } else if (staged) {
     // asynchronous 8-byte copies (all of a thread's loads in flight): lane = column,
     // warp = row
     const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
@@ -798,7 +826,7 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
   __shared__ float sred[8];
   __shared__ int sbq[(kGridTile / kGridSB) * (kGridTile / kGridSB)];
   __shared__ float sbS[(kGridTile / kGridSB) * (kGridTile / kGridSB)];
-  const int TP = T + 1;                  // padded row stride: banks (row + col) mod 32
+  const int TP = T;                      // row stride, a multiple of 32: bank = column mod 32
   const int NSB = (T + kGridSB - 1) / kGridSB;      // sub-blocks per side
   int* are = sacc_i;
   int* aim = are + T * TP;
@@ -951,8 +979,58 @@ int degrid_parts(const Cube& cb) { return (int)((cb.max_M + 255) / 256); }
 int degrid_tiled_parts(const Cube& cb) { return cb.ntile_r * cb.ntile_c; }
 
 static size_t degrid_tiled_smem(const Cube& cb) {
-  const int R = cb.tile + kTaps - 1, SP = ((R + 14) / 16) * 16 + 1;
-  return (size_t)R * SP * sizeof(float2);
+  return (size_t)(cb.tile + kTaps - 1) * degrid_stage_stride(cb.tile) * sizeof(float2);
+}
+
+// TMA descriptors for the degridder's staging (see k_degrid_tiled): the grid scratch
+// of a cube viewed as a 4-D tensor of 8-byte elements, dims (K2, N2c, N1c, L) with
+// row index r * N2c + t, boxes (S, 1, T, 1) and (S, 1, 6, 1).  A cube whose geometry
+// does not fit (or a driver without the entry point) keeps the asynchronous copies.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+void encode_degrid_maps(fhs_ctx* ctx) {
+  static EncodeTiledFn encode = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      encode = (EncodeTiledFn)fn;
+  }
+  for (Cube& cb : ctx->cubes) {
+    cb.tma = false;
+    const int T = cb.tile, S = degrid_stage_stride(T);
+    // the tile rows must lie in one t-slice of the view and the box must fit the grid
+    const bool geom = (cb.N2c == 1 || cb.N1c == T) && T + kTaps - 1 <= 256 && S <= 256 && S <= cb.K2 &&
+                      ((uintptr_t)ctx->s.grid % 16) == 0;
+    if (!encode || !geom) continue;
+    cuuint64_t dims[4] = {(cuuint64_t)cb.K2, (cuuint64_t)cb.N2c, (cuuint64_t)cb.N1c, (cuuint64_t)cb.L};
+    cuuint64_t strides[3] = {(cuuint64_t)cb.K2 * 8, (cuuint64_t)cb.N2c * cb.K2 * 8, (cuuint64_t)cb.K1 * cb.K2 * 8};
+    cuuint32_t box_rows[4] = {(cuuint32_t)S, 1, (cuuint32_t)T, 1};
+    cuuint32_t box_halo[4] = {(cuuint32_t)S, 1, (cuuint32_t)(kTaps - 1), 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r1 = encode(&cb.tm_rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)ctx->s.grid, dims, strides,
+                         box_rows, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r2 = encode(&cb.tm_halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)ctx->s.grid, dims, strides,
+                         box_halo, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    cb.tma = (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS);
+  }
+}
+
+unsigned read_device_status(bool clear) {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_dev_status, sizeof(v)) != cudaSuccess) return 0;
+  if (clear && v) {
+    const unsigned z = 0;
+    cudaMemcpyToSymbol(g_dev_status, &z, sizeof(z));
+  }
+  return v;
 }
 
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st) {
@@ -960,7 +1038,8 @@ void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, 
     dim3 grd(degrid_tiled_parts(cb), cb.L);
     k_degrid_tiled<0><<<grd, 256, degrid_tiled_smem(cb), st>>>(grid, cb.d_uv, cb.d_tile_off, cb.d_vis_off,
                                                                vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, out,
-                                                               nullptr, nullptr, nullptr, nullptr, cb.B, nullptr);
+                                                               nullptr, nullptr, nullptr, nullptr, cb.B, nullptr,
+                                                               cb.tm_rows, cb.tm_halo, cb.tma ? 1 : 0);
   } else {
     dim3 grd(degrid_parts(cb), cb.L);
     k_degrid<<<grd, 256, 0, st>>>(grid, cb.d_uv, out, cb.d_vis_off, vis_geom(cb));
@@ -973,7 +1052,8 @@ void launch_degrid_pdfb_tiled(const Cube& cb, const float2* grid, const float2* 
   dim3 grd(degrid_tiled_parts(cb), cb.L);
   k_degrid_tiled<1><<<grd, 256, degrid_tiled_smem(cb), st>>>(grid, cb.d_uv, cb.d_tile_off, cb.d_vis_off,
                                                              vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, d_out, y,
-                                                             v, u_prev, cb.d_blk, cb.B, partials);
+                                                             v, u_prev, cb.d_blk, cb.B, partials, cb.tm_rows,
+                                                             cb.tm_halo, cb.tma ? 1 : 0);
   note_launches(1);
 }
 
@@ -1010,7 +1090,7 @@ void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, flo
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
-  size_t sm = 2 * (size_t)cb.tile * (cb.tile + 1) * sizeof(int);
+  size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(int);
   k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
                                vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
