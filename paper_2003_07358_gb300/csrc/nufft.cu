@@ -916,8 +916,8 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
         val.y *= s;
       }
       if (pass == 0 && v_write) v_write[i] = val;
-      float wc[kTaps], xr;
-      const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
+      float wc[kTaps], wr[kTaps];
+      const int kr = kb_weights(w.y, vg.tc.hi_r, vg.tc.lo_r, wr);
       const int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
       // footprint start in the source tile, then the taps of quadrant (dr, dc)
       // relative to this tile: rows lr + a - dr T, a in [a0, a1)
@@ -932,14 +932,17 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
       const int asplit = (r0 + 1) * kGridSB - lr, bsplit = (c0 + 1) * kGridSB - lc;
       const float S00 = sbS[r0 * NSB + c0], S01 = sbS[r0 * NSB + c1];
       const float S10 = sbS[r1 * NSB + c0], S11 = sbS[r1 * NSB + c1];
-      // rolled row loop over all 7 rows (a warp-uniform, so the row weight's constant-
-      // bank coefficients are broadcast); rows outside [a0, a1) are skipped
+      // rolled row loop over all 7 rows; the row weights were evaluated once above and
+      // are rotated through wr[0] (no dynamic register indexing); rows outside [a0, a1)
+      // are skipped
 #pragma unroll 1
       for (int a = 0; a < kTaps; ++a) {
+        const float wa = wr[0];
+#pragma unroll
+        for (int j = 0; j < kTaps - 1; ++j) wr[j] = wr[j + 1];
         if (a < a0 || a >= a1) continue;
         const bool top = a < asplit;
         const float Sa = top ? S00 : S10, Sb = top ? S01 : S11;
-        const float wa = kb_tap(a, xr);
         const float va0 = wa * val.x * Sa, vb0 = wa * val.y * Sa;
         const float va1 = wa * val.x * Sb, vb1 = wa * val.y * Sb;
         int* pr = are + (lr + a) * TP + lc;
