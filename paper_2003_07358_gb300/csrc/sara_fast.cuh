@@ -48,47 +48,27 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // ------------------------------------------------------------- analysis
+// x then y pass of one (basis, level) for the coefficient tile (k0, c0) of one channel.
+// Staged input element (r, c) of this filter's window is tin[r + o][c + o] (o > 0 when
+// the window sits inside a wider one staged for a longer filter).  Writes the three
+// detail bands (/3) to cl + off_d and the LL band to llo (next level's input) or, when
+// llo is null, to cl + off_ll (/3).  Starts with a barrier so that tlx / thx may be
+// reused from a previous call.
 template <int F>
-__global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, float* __restrict__ ll_out,
-                                              float* __restrict__ coef, int64_t I, int64_t off0, int64_t off1,
-                                              int64_t off2, int64_t off_ll, int m1, int m2, int mo1, int mo2) {
+__device__ __forceinline__ void ana_tile(const float (*tin)[kIn2 + 1], int o, float (*tlx)[kT2 + 1],
+                                         float (*thx)[kT2 + 1], float* __restrict__ cl, float* __restrict__ llo,
+                                         int64_t off0, int64_t off1, int64_t off2, int64_t off_ll, int k0, int c0,
+                                         int mo1, int mo2) {
   constexpr int IN = 2 * kT2 + F - 2;
   constexpr int WIN = F + 6;                          // window of a 4-output block
-  __shared__ float tin[kIn2][kIn2 + 1];
-  __shared__ float tlx[kIn2][kT2 + 1];
-  __shared__ float thx[kIn2][kT2 + 1];
   FTaps<F> f;
-  f.load();
-  const int l = blockIdx.z;
-  const int k0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
-  const int r_in0 = 2 * k0 + 2 - F, c_in0 = 2 * c0 + 2 - F;
-  const float* inl = in + (size_t)l * m1 * m2;
-  // stage the input tile with asynchronous copies (zero fill outside the image), so
-  // that all of a thread's loads are in flight at once: lane = column, warp = row
-  {
-    const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
-#pragma unroll
-    for (int cj = 0; cj < (IN + 31) / 32; ++cj) {
-      const int c = lane + 32 * cj, gc = c_in0 + c;
-      if (c >= IN) continue;
-      const bool vc = gc >= 0 && gc < m2;
-#pragma unroll 4
-      for (int r = wrp; r < IN; r += 8) {
-        const int gr = r_in0 + r;
-        const bool v = vc && gr >= 0 && gr < m1;
-        cp_async4(&tin[r][c], v ? inl + (size_t)gr * m2 + gc : inl, v);
-      }
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-  }
   __syncthreads();
   // x: lx[r][kc] = sum_t h[t] tin[r][2 kc + F - 1 - t], 4 consecutive kc per item
   for (int item = threadIdx.x; item < IN * 8; item += 256) {
     const int r = item >> 3, kc0 = (item & 7) * 4;
     float v[WIN];
 #pragma unroll
-    for (int u = 0; u < WIN; ++u) v[u] = tin[r][2 * kc0 + u];
+    for (int u = 0; u < WIN; ++u) v[u] = tin[r + o][2 * kc0 + u + o];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       float sl = 0.f, sh = 0.f;
@@ -103,39 +83,112 @@ __global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, floa
   }
   __syncthreads();
   // y: 4 consecutive coefficient rows per thread, all four bands
-  {
-    const int kc = threadIdx.x & 31, kr0 = (threadIdx.x >> 5) * 4;
-    float a[WIN], b[WIN];
+  const int kc = threadIdx.x & 31, kr0 = (threadIdx.x >> 5) * 4;
+  float a[WIN], b[WIN];
 #pragma unroll
-    for (int u = 0; u < WIN; ++u) {
-      a[u] = tlx[2 * kr0 + u][kc];
-      b[u] = thx[2 * kr0 + u][kc];
+  for (int u = 0; u < WIN; ++u) {
+    a[u] = tlx[2 * kr0 + u][kc];
+    b[u] = thx[2 * kr0 + u][kc];
+  }
+  const float third = 1.f / 3.f;
+  const int gc = c0 + kc;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float ll = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+    for (int t = 0; t < F; ++t) {
+      const float va = a[2 * m + F - 1 - t], vb = b[2 * m + F - 1 - t];
+      ll = fmaf(f.h[t], va, ll);
+      d1 = fmaf(f.g[t], va, d1);
+      d0 = fmaf(f.h[t], vb, d0);
+      d2 = fmaf(f.g[t], vb, d2);
     }
-    const float third = 1.f / 3.f;
-    const int gc = c0 + kc;
-    float* cl = coef + (size_t)l * I;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      float ll = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-#pragma unroll
-      for (int t = 0; t < F; ++t) {
-        const float va = a[2 * m + F - 1 - t], vb = b[2 * m + F - 1 - t];
-        ll = fmaf(f.h[t], va, ll);
-        d1 = fmaf(f.g[t], va, d1);
-        d0 = fmaf(f.h[t], vb, d0);
-        d2 = fmaf(f.g[t], vb, d2);
-      }
-      const int gk = k0 + kr0 + m;
-      if (gk < mo1 && gc < mo2) {
-        const int64_t pos = (int64_t)gk * mo2 + gc;
-        cl[off0 + pos] = d0 * third;
-        cl[off1 + pos] = d1 * third;
-        cl[off2 + pos] = d2 * third;
-        if (ll_out) ll_out[(size_t)l * mo1 * mo2 + pos] = ll;
-        else cl[off_ll + pos] = ll * third;
-      }
+    const int gk = k0 + kr0 + m;
+    if (gk < mo1 && gc < mo2) {
+      const int64_t pos = (int64_t)gk * mo2 + gc;
+      cl[off0 + pos] = d0 * third;
+      cl[off1 + pos] = d1 * third;
+      cl[off2 + pos] = d2 * third;
+      if (llo) llo[pos] = ll;
+      else cl[off_ll + pos] = ll * third;
     }
   }
+}
+
+// Stage rows [r0, r0 + IN) x columns [c0, c0 + IN) of one channel image (zero outside)
+// with asynchronous copies, so that all of a thread's loads are in flight at once:
+// lane = column, warp = row.
+template <int IN>
+__device__ __forceinline__ void ana_stage(float (*tin)[kIn2 + 1], const float* __restrict__ inl, int r0, int c0,
+                                          int m1, int m2) {
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
+#pragma unroll
+  for (int cj = 0; cj < (IN + 31) / 32; ++cj) {
+    const int c = lane + 32 * cj, gc = c0 + c;
+    if (c >= IN) continue;
+    const bool vc = gc >= 0 && gc < m2;
+#pragma unroll 4
+    for (int r = wrp; r < IN; r += 8) {
+      const int gr = r0 + r;
+      const bool v = vc && gr >= 0 && gr < m1;
+      cp_async4(&tin[r][c], v ? inl + (size_t)gr * m2 + gc : inl, v);
+    }
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+}
+
+// One (basis, level) for a 32x32 coefficient tile of one channel.
+template <int F>
+__global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, float* __restrict__ ll_out,
+                                              float* __restrict__ coef, int64_t I, int64_t off0, int64_t off1,
+                                              int64_t off2, int64_t off_ll, int m1, int m2, int mo1, int mo2) {
+  __shared__ float tin[kIn2][kIn2 + 1];
+  __shared__ float tlx[kIn2][kT2 + 1];
+  __shared__ float thx[kIn2][kT2 + 1];
+  const int l = blockIdx.z;
+  const int k0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
+  ana_stage<2 * kT2 + F - 2>(tin, in + (size_t)l * m1 * m2, 2 * k0 + 2 - F, 2 * c0 + 2 - F, m1, m2);
+  ana_tile<F>(tin, 0, tlx, thx, coef + (size_t)l * I, ll_out ? ll_out + (size_t)l * mo1 * mo2 : nullptr, off0, off1,
+              off2, off_ll, k0, c0, mo1, mo2);
+}
+
+// Level 1 of all eight bases for a 32x32 coefficient tile of one channel: the input
+// window of the longest filter (db8, 78 x 78) is staged once and each basis reads its
+// own window inside it (offset 16 - F), instead of one launch and one staging per
+// basis.  The LL1 band of basis b goes to its slot in the LL1 buffer (the input of
+// its level 2).
+struct Ana1 {
+  int64_t off[8][3];   // level-1 detail-band offsets of each basis
+  int mo1[8], mo2[8];  // level-1 coefficient rows / columns of each basis
+  int64_t ll_off[8];   // LL1 slot of each basis in the LL1 buffer (units of floats)
+};
+
+template <int F>
+__device__ __forceinline__ void ana1_basis(const Ana1& a, const float (*tin)[kIn2 + 1], float (*tlx)[kT2 + 1],
+                                           float (*thx)[kT2 + 1], float* cl, float* ll1, int l, int k0, int c0) {
+  constexpr int b = F / 2 - 1;
+  ana_tile<F>(tin, kMaxFilt - F, tlx, thx, cl, ll1 + a.ll_off[b] + (size_t)l * a.mo1[b] * a.mo2[b], a.off[b][0],
+              a.off[b][1], a.off[b][2], 0, k0, c0, a.mo1[b], a.mo2[b]);
+}
+
+__global__ void __launch_bounds__(256) k_ana1_all(const float* __restrict__ x, float* __restrict__ coef,
+                                                  float* __restrict__ ll1, Ana1 a, int64_t I, int n1, int n2) {
+  __shared__ float tin[kIn2][kIn2 + 1];
+  __shared__ float tlx[kIn2][kT2 + 1];
+  __shared__ float thx[kIn2][kT2 + 1];
+  const int l = blockIdx.z;
+  const int k0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
+  ana_stage<kIn2>(tin, x + (size_t)l * n1 * n2, 2 * k0 + 2 - kMaxFilt, 2 * c0 + 2 - kMaxFilt, n1, n2);
+  float* cl = coef + (size_t)l * I;
+  ana1_basis<2>(a, tin, tlx, thx, cl, ll1, l, k0, c0);
+  ana1_basis<4>(a, tin, tlx, thx, cl, ll1, l, k0, c0);
+  ana1_basis<6>(a, tin, tlx, thx, cl, ll1, l, k0, c0);
+  ana1_basis<8>(a, tin, tlx, thx, cl, ll1, l, k0, c0);
+  ana1_basis<10>(a, tin, tlx, thx, cl, ll1, l, k0, c0);
+  ana1_basis<12>(a, tin, tlx, thx, cl, ll1, l, k0, c0);
+  ana1_basis<14>(a, tin, tlx, thx, cl, ll1, l, k0, c0);
+  ana1_basis<16>(a, tin, tlx, thx, cl, ll1, l, k0, c0);
 }
 
 // ---------------------------------------------------------- l2,1 dual
@@ -403,9 +456,32 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
   float* coef = ctx->s.coef;
   float* llA = ctx->s.t2;
   float* llB = ctx->s.t3;
+  // LL1 slots of the eight bases (also read by the synthesis below)
+  {
+    int64_t off = 0;
+    for (int b = 0; b < 8; ++b) {
+      ctx->s.ll1_off[b] = off;
+      off += (int64_t)L * S.rows[b][1] * S.cols[b][1];
+    }
+  }
+  // level 1 of every basis in one launch (grid over the longest filter's coefficients)
+  {
+    Ana1 a;
+    for (int b = 0; b < 8; ++b) {
+      for (int k = 0; k < 3; ++k) a.off[b][k] = S.off[b][1][k];
+      a.mo1[b] = S.rows[b][1];
+      a.mo2[b] = S.cols[b][1];
+      a.ll_off[b] = ctx->s.ll1_off[b];
+    }
+    int r = 0, c = 0;
+    for (int b = 0; b < 8; ++b) { r = std::max(r, S.rows[b][1]); c = std::max(c, S.cols[b][1]); }
+    dim3 g((c + kT2 - 1) / kT2, (r + kT2 - 1) / kT2, L);
+    k_ana1_all<<<g, 256, 0, st>>>(x, coef, ctx->s.ll1, a, S.I, cb.n1, cb.n2);
+    note_launches(1);
+  }
   for (int b = 0; b < 8; ++b) {
-    const float* in = x;
-    for (int j = 1; j <= kLevels; ++j) {
+    const float* in = ctx->s.ll1 + ctx->s.ll1_off[b];
+    for (int j = 2; j <= kLevels; ++j) {
       float* llo = (j == kLevels) ? nullptr : ((j & 1) ? llA : llB);
       FHS_BASIS_SWITCH(b, ana2_launch, cb, b, j, in, llo, coef, st);
       in = llo;
