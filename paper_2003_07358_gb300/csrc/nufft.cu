@@ -636,13 +636,25 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
     asm volatile("cp.async.wait_group 0;\n" ::);
   }
   __syncthreads();
+  // the next iteration's uv is loaded one iteration ahead (its latency overlaps the taps)
+  float2 w_next = beg + (int)threadIdx.x < end ? uv[vbase + beg + threadIdx.x] : make_float2(0.f, 0.f);
   for (int base = beg; base < end; base += blockDim.x) {
     const int k = base + threadIdx.x;
     const bool valid = k < end;
     const int64_t i = vbase + k;
+    const float2 w = w_next;
+    if (k + (int)blockDim.x < end) w_next = uv[i + blockDim.x];
+    // the data-step operands are issued before the taps
+    float2 yy = make_float2(0.f, 0.f), vv = yy, up = yy;
+    int bk = -1;
+    if (MODE == 1 && valid) {
+      yy = y[i];
+      vv = v[i];
+      up = u_prev[i];
+      bk = blk[i];
+    }
     float2 u = make_float2(0.f, 0.f);
     if (valid) {
-      const float2 w = uv[i];
       float wc[kTaps], xr;
       const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
       const int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
@@ -674,12 +686,11 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
     double v0 = 0.0, v1 = 0.0;
     int b = -1;
     if (valid) {
-      const float2 yy = y[i], vv = v[i], up = u_prev[i];
       const float2 z = make_float2(vv.x + 2.f * u.x - up.x, vv.y + 2.f * u.y - up.y);
       const float2 d = make_float2(z.x - yy.x, z.y - yy.y);
       out[i] = d;
       u_prev[i] = u;
-      b = blk[i];
+      b = bk;
       v0 = (double)fmaf(d.x, d.x, d.y * d.y);
       const float rx = yy.x - u.x, ry = yy.y - u.y;
       v1 = (double)fmaf(rx, rx, ry * ry);
