@@ -812,10 +812,6 @@ __global__ void k_l2ball_scale(const float2* __restrict__ d, const float* __rest
 //   sweep 2: each tap adds rint(c S_sb) to its cell; the cell is read back as
 //            acc / S_sb (resolution 2^-29 of its sub-block's bound).
 constexpr int kGridSB = 8;                        // sub-block side (cells)
-constexpr int kSlot = 4 + 2 * kTaps + 1;          // words per staged visibility (odd: conflict-free)
-
-// Accumulator row stride of the gridder: T rounded up to 7 mod 32.
-__host__ __device__ inline int grid_row_stride(int T) { return T + ((7 - T % 32) + 32) % 32; }
 
 // Source range [beg, end) of pass (dr, dc) for destination tile (tr, tc).
 __device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, int tr, int tc, int ntr, int ntc,
@@ -841,10 +837,8 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
   __shared__ float sred[8];
   __shared__ int sbq[(kGridTile / kGridSB) * (kGridTile / kGridSB)];
   __shared__ float sbS[(kGridTile / kGridSB) * (kGridTile / kGridSB)];
-  const int TP = grid_row_stride(T);     // = 7 mod 32 (see sweep 2)
+  const int TP = T;                      // row stride, a multiple of 32: bank = column mod 32
   const int NSB = (T + kGridSB - 1) / kGridSB;      // sub-blocks per side
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __shared__ float slots[8][32 * kSlot];
   int* are = sacc_i;
   int* aim = are + T * TP;
   const int l = blockIdx.y;
@@ -918,67 +912,59 @@ __global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals
     sbS[k] = S;
   }
   __syncthreads();
-  // ---- sweep 2: taps, warp-cooperative.  A warp takes its visibilities 32 at a time:
-  // each lane evaluates one visibility's 14 Kaiser-Bessel weights and footprint origin
-  // into the warp's slots, then the warp walks the 32 slots with lane = tap (taps
-  // 0..31, then 32..48).  With the row stride TP = 7 mod 32 the bank of tap
-  // (a, b) = 7a + b is the tap index plus a constant: every atomic instruction touches
-  // distinct banks.
-  {
-    float* sl = slots[wid];
-    // this lane's taps in the two rounds
-    const int ta0 = lane / kTaps, tb0 = lane - ta0 * kTaps;
-    const int t1 = lane + 32, ta1 = t1 / kTaps, tb1 = t1 - ta1 * kTaps;
-    const bool r1 = t1 < kTaps * kTaps;
-    for (int pass = 0; pass < 4; ++pass) {
-      const int dr = pass >> 1, dc = pass & 1;
-      int sr, sc, beg, end;
-      grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
-      for (int bt = beg + 32 * wid; bt < end; bt += 32 * 8) {
-        const int k = bt + lane;
-        const int nv = min(32, end - bt);
-        if (k < end) {
-          const int64_t i = vbase + k;
-          const float2 w = uv[i];
-          float2 val = vals[i];
-          if (blk_scale) {
-            const float sb = blk_scale[l * B + blk[i]];
-            val.x *= sb;
-            val.y *= sb;
-          }
-          if (pass == 0 && v_write) v_write[i] = val;
-          float wr[kTaps], wc[kTaps];
-          const int kr = kb_weights(w.y, vg.tc.hi_r, vg.tc.lo_r, wr);
-          const int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
-          float* my = sl + lane * kSlot;
-          my[0] = __int_as_float((kr & (vg.K1 - 1)) - sr * T - dr * T);   // footprint origin in this tile
-          my[1] = __int_as_float((kc & (vg.K2 - 1)) - sc * T - dc * T);
-          my[2] = val.x;
-          my[3] = val.y;
+  // ---- sweep 2: taps
+  for (int pass = 0; pass < 4; ++pass) {
+    const int dr = pass >> 1, dc = pass & 1;
+    int sr, sc, beg, end;
+    grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
+    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
+      const int64_t i = vbase + k;
+      float2 w = uv[i];
+      float2 val = vals[i];
+      if (blk_scale) {
+        float s = blk_scale[l * B + blk[i]];
+        val.x *= s;
+        val.y *= s;
+      }
+      if (pass == 0 && v_write) v_write[i] = val;
+      float wc[kTaps], wr[kTaps];
+      const int kr = kb_weights(w.y, vg.tc.hi_r, vg.tc.lo_r, wr);
+      const int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
+      // footprint start in the source tile, then the taps of quadrant (dr, dc)
+      // relative to this tile: rows lr + a - dr T, a in [a0, a1)
+      const int lr = (kr & (vg.K1 - 1)) - sr * T - dr * T;
+      const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
+      const int a0 = max(0, -lr), a1 = min(kTaps, T - lr);
+      const int b0 = max(0, -lc), b1 = min(kTaps, T - lc);
+      // the footprint spans at most two sub-blocks per axis: a < asplit (b < bsplit)
+      // takes the first; the four scales are read once per visibility
+      const int r0 = min(max(lr, 0) / kGridSB, NSB - 1), c0 = min(max(lc, 0) / kGridSB, NSB - 1);
+      const int r1 = min(r0 + 1, NSB - 1), c1 = min(c0 + 1, NSB - 1);
+      const int asplit = (r0 + 1) * kGridSB - lr, bsplit = (c0 + 1) * kGridSB - lc;
+      const float S00 = sbS[r0 * NSB + c0], S01 = sbS[r0 * NSB + c1];
+      const float S10 = sbS[r1 * NSB + c0], S11 = sbS[r1 * NSB + c1];
+      // rolled row loop over all 7 rows; the row weights were evaluated once above and
+      // are rotated through wr[0] (no dynamic register indexing); rows outside [a0, a1)
+      // are skipped
+#pragma unroll 1
+      for (int a = 0; a < kTaps; ++a) {
+        const float wa = wr[0];
 #pragma unroll
-          for (int j = 0; j < kTaps; ++j) {
-            my[4 + j] = wr[j];
-            my[4 + kTaps + j] = wc[j];
-          }
-        }
-        __syncwarp();
-        for (int j = 0; j < nv; ++j) {
-          const float* q = sl + j * kSlot;
-          const int lr = __float_as_int(q[0]), lc = __float_as_int(q[1]);
-          const float vx = q[2], vy = q[3];
+        for (int j = 0; j < kTaps - 1; ++j) wr[j] = wr[j + 1];
+        if (a < a0 || a >= a1) continue;
+        const bool top = a < asplit;
+        const float Sa = top ? S00 : S10, Sb = top ? S01 : S11;
+        const float va0 = wa * val.x * Sa, vb0 = wa * val.y * Sa;
+        const float va1 = wa * val.x * Sb, vb1 = wa * val.y * Sb;
+        int* pr = are + (lr + a) * TP + lc;
+        int* pi = aim + (lr + a) * TP + lc;
 #pragma unroll
-          for (int rnd = 0; rnd < 2; ++rnd) {
-            const int a = rnd ? ta1 : ta0, b = rnd ? tb1 : tb0;
-            if (rnd && !r1) continue;
-            const int row = lr + a, col = lc + b;
-            if (row < 0 || row >= T || col < 0 || col >= T) continue;   // taps of other tiles / passes
-            const float S = sbS[(row / kGridSB) * NSB + col / kGridSB];
-            const float wgt = q[4 + a] * q[4 + kTaps + b] * S;
-            atomicAdd(&are[row * TP + col], __float2int_rn(wgt * vx));
-            atomicAdd(&aim[row * TP + col], __float2int_rn(wgt * vy));
-          }
+        for (int b = 0; b < kTaps; ++b) {
+          if (b < b0 || b >= b1) continue;
+          const bool first = b < bsplit;
+          atomicAdd(pr + b, __float2int_rn(wc[b] * (first ? va0 : va1)));
+          atomicAdd(pi + b, __float2int_rn(wc[b] * (first ? vb0 : vb1)));
         }
-        __syncwarp();
       }
     }
   }
@@ -1118,7 +1104,7 @@ void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, flo
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
-  size_t sm = 2 * (size_t)cb.tile * grid_row_stride(cb.tile) * sizeof(int);
+  size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(int);
   k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
                                vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
