@@ -63,6 +63,7 @@ struct Cube {
   int64_t* d_perm = nullptr;                 // [n_vis]
   int32_t* d_tile_off = nullptr;             // [L][ntiles*4 + 1] per-channel tile/class offsets (relative)
   int ntile_r, ntile_c, tile;                // gridder tiles
+  int* d_ncmax = nullptr;                    // [L][ntiles] most footprints covering one cell of a tile
   // device copies of per-cube parameters and tables
   NucFacet* d_facets = nullptr;
   float* d_win = nullptr;                    // window tables (y and x windows concatenated)
@@ -158,6 +159,7 @@ void launch_block_finalize(const Cube& cb, const double* partials, int nparts, f
 int host_first_tap(float om, int K);
 void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write,
                  float2* grid, cudaStream_t st);
+void launch_grid_count(const Cube& cb, cudaStream_t st);
 void launch_l2ball_partials(const Cube& cb, const float2* z, const float2* y, float2* d,
                             double* partials, int nparts, cudaStream_t st);
 void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, float2* v, cudaStream_t st);

@@ -485,12 +485,17 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
   upload(cb.d_eps, cb.eps.data(), cb.eps.size(), st);
   upload(cb.d_eta, eta_f.data(), eta_f.size(), st);
   upload(cb.d_mubar, mub_f.data(), mub_f.size(), st);
+  // per grid tile, the most footprints that cover one of its cells (fixes the
+  // gridder's fixed-point scale; depends on the uv coverage only)
+  cb.d_ncmax = dalloc<int>((size_t)d.L * cb.ntile_r * cb.ntile_c);
+  launch_grid_count(cb, st);
+  FHS_CUDA(cudaGetLastError());
   FHS_CUDA(cudaStreamSynchronize(st));
 }
 
 void free_cube(Cube& cb) {
   void* ps[] = {cb.d_uv, cb.d_blk, cb.d_perm, cb.d_vis_off, cb.d_tile_off, cb.d_facets, cb.d_win, cb.d_win64, cb.d_tile_of,
-                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar};
+                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar, cb.d_ncmax};
   for (void* p : ps)
     if (p) cudaFree(p);
 }

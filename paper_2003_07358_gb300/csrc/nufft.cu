@@ -578,6 +578,16 @@ __global__ void __launch_bounds__(256) k_degrid_pdfb(const float2* __restrict__ 
 // and written once per CTA: partials[l][tile][2][B].
 constexpr int kDegStageMin = 96;
 
+// acc (hi, lo) += x with an exact TwoSum of hi and x (Knuth): the pair carries the
+// sum to about 2^-48 of its magnitude.
+__device__ __forceinline__ void ff_accum(float2& acc, float x) {
+  const float s = __fadd_rn(acc.x, x);
+  const float bp = __fadd_rn(s, -acc.x);
+  const float e = __fadd_rn(__fadd_rn(acc.x, -__fadd_rn(s, -bp)), __fadd_rn(x, -bp));
+  acc.x = s;
+  acc.y = __fadd_rn(acc.y, e);
+}
+
 // Staged row stride of the degridder (float2): T + 6 rounded up to 16.
 __host__ __device__ inline int degrid_stage_stride(int T) { return ((T + kTaps - 1 + 15) / 16) * 16; }
 
@@ -592,7 +602,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
                                                       const __grid_constant__ CUtensorMap tm_rows,
                                                       const __grid_constant__ CUtensorMap tm_halo, int use_tma) {
   extern __shared__ __align__(128) float2 sg[];
-  __shared__ double sacc[8][2][kMaxB];
+  __shared__ float2 sacc[8][2][kMaxB];   // per warp, per block: float-float (hi, lo) sums
   __shared__ __align__(8) uint64_t bar;
   const int l = blockIdx.y, tau = blockIdx.x;
   const int tr = tau / ntc, tc = tau % ntc;
@@ -601,7 +611,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
   const int64_t vbase = vis_off[l];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (MODE == 1) {
-    for (int k = threadIdx.x; k < 8 * 2 * kMaxB; k += blockDim.x) (&sacc[0][0][0])[k] = 0.0;
+    for (int k = threadIdx.x; k < 8 * 2 * kMaxB; k += blockDim.x) (&sacc[0][0][0])[k] = make_float2(0.f, 0.f);
   }
   const float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
   const int R = T + kTaps - 1, SP = degrid_stage_stride(T);
@@ -683,7 +693,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
       if (valid) out[i] = u;
       continue;
     }
-    double v0 = 0.0, v1 = 0.0;
+    float v0 = 0.f, v1 = 0.f;
     int b = -1;
     if (valid) {
       const float2 z = make_float2(vv.x + 2.f * u.x - up.x, vv.y + 2.f * u.y - up.y);
@@ -691,24 +701,27 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
       out[i] = d;
       u_prev[i] = u;
       b = bk;
-      v0 = (double)fmaf(d.x, d.x, d.y * d.y);
+      v0 = fmaf(d.x, d.x, d.y * d.y);
       const float rx = yy.x - u.x, ry = yy.y - u.y;
-      v1 = (double)fmaf(rx, rx, ry * ry);
+      v1 = fmaf(rx, rx, ry * ry);
     }
     // valid lanes form a prefix of the CTA, so lane 0 invalid means the warp is idle
     const int b0 = __shfl_sync(0xffffffffu, b, 0);
     if (b0 < 0) continue;
     const bool uniform = __all_sync(0xffffffffu, b < 0 || b == b0);
+    // FP32 tree over the 32 lanes (fixed order), then lane 0 adds the warp's sum to its
+    // float-float accumulator: no FP64 arithmetic per visibility (FP64 runs at a small
+    // fraction of the FP32 rate on this GPU); FP64 takes over at the CTA sum below
     for (int bb = uniform ? b0 : 0; bb < (uniform ? b0 + 1 : B); ++bb) {
-      double s0 = (b == bb) ? v0 : 0.0, s1 = (b == bb) ? v1 : 0.0;
+      float s0 = (b == bb) ? v0 : 0.f, s1 = (b == bb) ? v1 : 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       }
       if (lane == 0) {
-        sacc[wid][0][bb] += s0;
-        sacc[wid][1][bb] += s1;
+        ff_accum(sacc[wid][0][bb], s0);
+        ff_accum(sacc[wid][1][bb], s1);
       }
     }
   }
@@ -718,7 +731,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
   for (int k = threadIdx.x; k < 2 * B; k += blockDim.x) {
     const int c = k / B, bb = k - c * B;
     double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += sacc[w][c][bb];
+    for (int w = 0; w < 8; ++w) s += (double)sacc[w][c][bb].x + (double)sacc[w][c][bb].y;
     po[k] = s;
   }
 }
@@ -802,16 +815,12 @@ __global__ void k_l2ball_scale(const float2* __restrict__ d, const float* __rest
 // and right, 3 crosses right only.
 // Accumulation is in fixed point with 32-bit integer shared-memory atomics (several
 // times faster than floating-point ones, and order-independent, so the result is
-// bitwise deterministic), with one scale per 8 x 8 sub-block of the tile:
-//   sweep 0: m = max over the CTA's visibilities of max(|Re v|, |Im v|);
-//   sweep 1: every visibility adds q = ceil(max(|Re v|, |Im v|) 2^qb / m) (an integer
-//            upper bound of its magnitude) to the sub-blocks its 7 x 7 footprint
-//            touches in this tile (qb chosen so that no counter can overflow);
-//   then bound_sb = sum q * m / 2^qb >= |any cell sum of the sub-block| (Kaiser-Bessel
-//   weights are <= 1) and S_sb = 2^e with bound_sb * S_sb < 2^29;
-//   sweep 2: each tap adds rint(c S_sb) to its cell; the cell is read back as
-//            acc / S_sb (resolution 2^-29 of its sub-block's bound).
-constexpr int kGridSB = 8;                        // sub-block side (cells)
+// bitwise deterministic), with one scale S = 2^e per tile chosen so that
+// n_c |c| < 2^30 for every tap value c = w v S, with n_c the largest number of
+// footprints that cover one cell of the tile (counted once per context, MODE 1) and
+// |v| <= m = max over the tile's visibilities of max(|Re v|, |Im v|): no cell can
+// overflow, and the resolution is n_c m / 2^30 (about 2^-23 of m for the densest
+// tiles of the large workload, n_c ~ 100).
 
 // Source range [beg, end) of pass (dr, dc) for destination tile (tr, tc).
 __device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, int tr, int tc, int ntr, int ntc,
@@ -828,151 +837,144 @@ __device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, i
 
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((unsigned)(e + 127) << 23); }
 
-__global__ void __launch_bounds__(256, 3) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
+// Adds the 7 x 7 taps of one visibility to the tile accumulators: rows lr + a,
+// columns lc + b.  ra[a] = row weight * S, wc[b] = column weight, (vx, vy) = v.
+// INTERIOR: the whole footprint lies in the tile (no bounds tests); otherwise only
+// rows in [a0, a1) and columns in [b0, b1) are added.  MODE 1 adds 1 per tap.
+template <bool INTERIOR, int MODE>
+__device__ __forceinline__ void grid_taps(int* are, int* aim, int TP, int lr, int lc, const float* ra,
+                                          const float* wc, float vx, float vy, int a0, int a1, int b0, int b1) {
+#pragma unroll
+  for (int a = 0; a < kTaps; ++a) {
+    if (!INTERIOR && (a < a0 || a >= a1)) continue;
+    int* pr = are + (lr + a) * TP + lc;
+    int* pi = aim + (lr + a) * TP + lc;
+    const float xr = vx * ra[a], xi = vy * ra[a];
+#pragma unroll
+    for (int b = 0; b < kTaps; ++b) {
+      if (!INTERIOR && (b < b0 || b >= b1)) continue;
+      if (MODE == 1) {
+        atomicAdd(pr + b, 1);
+      } else {
+        atomicAdd(pr + b, __float2int_rn(wc[b] * xr));
+        atomicAdd(pi + b, __float2int_rn(wc[b] * xi));
+      }
+    }
+  }
+}
+
+// MODE 0: grid the (block-scaled) values into the tile and store it; MODE 1 (once per
+// context): count the footprints covering each cell and store the tile's maximum in
+// ncmax[l][tile].
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
                                               float2* __restrict__ v_write, const float2* __restrict__ uv,
                                               const uint8_t* __restrict__ blk, const int32_t* __restrict__ tile_off,
                                               const int64_t* __restrict__ vis_off, float2* __restrict__ grid,
-                                              VisGeom vg, int T, int ntr, int ntc, int B) {
-  extern __shared__ int sacc_i[];
+                                              int* __restrict__ ncmax, VisGeom vg, int T, int ntr, int ntc, int B) {
+  extern __shared__ __align__(16) int sacc_i[];
   __shared__ float sred[8];
-  __shared__ int sbq[(kGridTile / kGridSB) * (kGridTile / kGridSB)];
-  __shared__ float sbS[(kGridTile / kGridSB) * (kGridTile / kGridSB)];
+  __shared__ int sredi[8];
   const int TP = T;                      // row stride, a multiple of 32: bank = column mod 32
-  const int NSB = (T + kGridSB - 1) / kGridSB;      // sub-blocks per side
   int* are = sacc_i;
   int* aim = are + T * TP;
   const int l = blockIdx.y;
   const int tau = blockIdx.x;
   const int tr = tau / ntc, tc = tau % ntc;
-  for (int k = threadIdx.x; k < 2 * T * TP; k += blockDim.x) sacc_i[k] = 0;
-  for (int k = threadIdx.x; k < NSB * NSB; k += blockDim.x) sbq[k] = 0;
+  {
+    int4* z4 = reinterpret_cast<int4*>(sacc_i);
+    const int n4 = (MODE == 1 ? T * TP : 2 * T * TP) / 4;
+    for (int k = threadIdx.x; k < n4; k += blockDim.x) z4[k] = make_int4(0, 0, 0, 0);
+  }
   const int64_t vbase = vis_off[l];
   const int32_t* toff = tile_off + (size_t)l * (ntr * ntc * 4 + 1);
-  // ---- sweep 0: largest component magnitude and visibility count
-  float m = 0.f;
-  int cnt = 0;
-  for (int pass = 0; pass < 4; ++pass) {
-    int sr, sc, beg, end;
-    grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
-    cnt += end - beg;
-    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
-      const int64_t i = vbase + k;
-      const float2 val = vals[i];
-      const float s = blk_scale ? blk_scale[l * B + blk[i]] : 1.f;
-      m = fmaxf(m, fmaxf(fabsf(val.x * s), fabsf(val.y * s)));
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = m;
-  __syncthreads();
-  m = 0.f;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) m = fmaxf(m, sred[w]);
-  // qb: cnt * (2^qb + 1) < 2^30, so no counter can overflow (q <= 2^qb + 1 with the
-  // rounding of |v| / m); a tile without signal keeps every scale at 1
-  const int qb = max(0, min(20, 29 - (32 - __clz(cnt))));
-  const bool any = m > 1e-30f;
-  const float qscale = any ? pow2f(qb) / m : 0.f;
-  // ---- sweep 1: per sub-block upper bounds (integer, order-independent)
-  if (any) {
+  float S = 1.f;
+  if (MODE == 0) {
+    // ---- sweep 0: largest component magnitude over the visibilities touching the tile
+    float m = 0.f;
     for (int pass = 0; pass < 4; ++pass) {
-      const int dr = pass >> 1, dc = pass & 1;
       int sr, sc, beg, end;
       grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
       for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
         const int64_t i = vbase + k;
-        const float2 w = uv[i];
         const float2 val = vals[i];
         const float s = blk_scale ? blk_scale[l * B + blk[i]] : 1.f;
-        const int q = (int)ceilf(fmaxf(fabsf(val.x * s), fabsf(val.y * s)) * qscale);
-        float xr, xc;
-        const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
-        const int kc = kb_first(w.x, vg.tc.hi_c, vg.tc.lo_c, xc);
-        const int lr = (kr & (vg.K1 - 1)) - sr * T - dr * T;
-        const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
-        if (lr >= T || lc >= T || lr + kTaps <= 0 || lc + kTaps <= 0) continue;   // no tap here
-        const int r0 = max(lr, 0) / kGridSB, r1 = min(lr + kTaps - 1, T - 1) / kGridSB;
-        const int c0 = max(lc, 0) / kGridSB, c1 = min(lc + kTaps - 1, T - 1) / kGridSB;
-        for (int br = r0; br <= r1; ++br)
-          for (int bc = c0; bc <= c1; ++bc) atomicAdd(&sbq[br * NSB + bc], q);
+        m = fmaxf(m, fmaxf(fabsf(val.x * s), fabsf(val.y * s)));
       }
     }
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < NSB * NSB; k += blockDim.x) {
-    float S = 1.f;
-    if (any && sbq[k] > 0) {
-      // bound = sbq m / 2^qb (the 1.01 covers the roundings of q and of this product;
-      // an overflow to infinity only makes S small); S = 2^e with bound S < 2^29
-      const float bnd = (float)sbq[k] * m * pow2f(-qb) * 1.01f;
-      const int eb = (int)((__float_as_uint(bnd) >> 23) & 0xffu) - 126;   // bnd < 2^eb
-      S = pow2f(max(-100, min(29 - eb, 100)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m = fmaxf(m, sred[w]);
+    const int nc = ncmax[l * ntr * ntc + tau];
+    if (m > 1e-30f && nc > 0) {
+      // S = 2^e <= 2^30 / (n_c m'), m' = m (1 + 2^-10) covering the roundings of v s,
+      // of the row product and a kernel weight a hair above 1
+      const float t = 1073741824.f / ((float)nc * (m * 1.0009765625f));
+      const int e = (int)((__float_as_uint(t) >> 23) & 0xffu) - 127;   // 2^e <= t
+      S = pow2f(max(-120, min(e, 120)));
     }
-    sbS[k] = S;
+  } else {
+    __syncthreads();
   }
-  __syncthreads();
-  // ---- sweep 2: taps
+  // ---- sweep 1: taps
   for (int pass = 0; pass < 4; ++pass) {
     const int dr = pass >> 1, dc = pass & 1;
     int sr, sc, beg, end;
     grid_pass_range(toff, pass, tr, tc, ntr, ntc, sr, sc, beg, end);
+    // pass 0 starts with the interior class: every tap in the tile
+    const int ibeg = beg, iend = pass == 0 ? toff[(sr * ntc + sc) * 4 + 1] : beg;
     for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
       const int64_t i = vbase + k;
-      float2 w = uv[i];
-      float2 val = vals[i];
-      if (blk_scale) {
-        float s = blk_scale[l * B + blk[i]];
-        val.x *= s;
-        val.y *= s;
+      const float2 w = uv[i];
+      float2 val = make_float2(0.f, 0.f);
+      if (MODE == 0) {
+        val = vals[i];
+        if (blk_scale) {
+          const float s = blk_scale[l * B + blk[i]];
+          val.x *= s;
+          val.y *= s;
+        }
+        if (pass == 0 && v_write) v_write[i] = val;
       }
-      if (pass == 0 && v_write) v_write[i] = val;
-      float wc[kTaps], wr[kTaps];
-      const int kr = kb_weights(w.y, vg.tc.hi_r, vg.tc.lo_r, wr);
+      float wc[kTaps], ra[kTaps];
+      const int kr = kb_weights(w.y, vg.tc.hi_r, vg.tc.lo_r, ra);
       const int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
-      // footprint start in the source tile, then the taps of quadrant (dr, dc)
-      // relative to this tile: rows lr + a - dr T, a in [a0, a1)
+#pragma unroll
+      for (int a = 0; a < kTaps; ++a) ra[a] *= S;
+      // footprint start in the source tile, relative to this tile
       const int lr = (kr & (vg.K1 - 1)) - sr * T - dr * T;
       const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
-      const int a0 = max(0, -lr), a1 = min(kTaps, T - lr);
-      const int b0 = max(0, -lc), b1 = min(kTaps, T - lc);
-      // the footprint spans at most two sub-blocks per axis: a < asplit (b < bsplit)
-      // takes the first; the four scales are read once per visibility
-      const int r0 = min(max(lr, 0) / kGridSB, NSB - 1), c0 = min(max(lc, 0) / kGridSB, NSB - 1);
-      const int r1 = min(r0 + 1, NSB - 1), c1 = min(c0 + 1, NSB - 1);
-      const int asplit = (r0 + 1) * kGridSB - lr, bsplit = (c0 + 1) * kGridSB - lc;
-      const float S00 = sbS[r0 * NSB + c0], S01 = sbS[r0 * NSB + c1];
-      const float S10 = sbS[r1 * NSB + c0], S11 = sbS[r1 * NSB + c1];
-      // rolled row loop over all 7 rows; the row weights were evaluated once above and
-      // are rotated through wr[0] (no dynamic register indexing); rows outside [a0, a1)
-      // are skipped
-#pragma unroll 1
-      for (int a = 0; a < kTaps; ++a) {
-        const float wa = wr[0];
-#pragma unroll
-        for (int j = 0; j < kTaps - 1; ++j) wr[j] = wr[j + 1];
-        if (a < a0 || a >= a1) continue;
-        const bool top = a < asplit;
-        const float Sa = top ? S00 : S10, Sb = top ? S01 : S11;
-        const float va0 = wa * val.x * Sa, vb0 = wa * val.y * Sa;
-        const float va1 = wa * val.x * Sb, vb1 = wa * val.y * Sb;
-        int* pr = are + (lr + a) * TP + lc;
-        int* pi = aim + (lr + a) * TP + lc;
-#pragma unroll
-        for (int b = 0; b < kTaps; ++b) {
-          if (b < b0 || b >= b1) continue;
-          const bool first = b < bsplit;
-          atomicAdd(pr + b, __float2int_rn(wc[b] * (first ? va0 : va1)));
-          atomicAdd(pi + b, __float2int_rn(wc[b] * (first ? vb0 : vb1)));
-        }
+      if (k >= ibeg && k < iend) {
+        grid_taps<true, MODE>(are, aim, TP, lr, lc, ra, wc, val.x, val.y, 0, kTaps, 0, kTaps);
+      } else {
+        const int a0 = max(0, -lr), a1 = min(kTaps, T - lr);
+        const int b0 = max(0, -lc), b1 = min(kTaps, T - lc);
+        grid_taps<false, MODE>(are, aim, TP, lr, lc, ra, wc, val.x, val.y, a0, a1, b0, b1);
       }
     }
   }
   __syncthreads();
+  if (MODE == 1) {
+    int mx = 0;
+    for (int q = threadIdx.x; q < T * T; q += blockDim.x) mx = max(mx, are[(q / T) * TP + q % T]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sredi[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 0; w < 8; ++w) mx = max(mx, sredi[w]);
+      ncmax[l * ntr * ntc + tau] = mx;
+    }
+    return;
+  }
+  const float inv = 1.f / S;                                   // power of two: exact
   float2* gl = grid + (size_t)l * vg.K1 * vg.K2;
   for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
     const int rr = q / T, cc = q % T, o = rr * TP + cc;
-    const float inv = 1.f / sbS[(rr / kGridSB) * NSB + cc / kGridSB];    // power of two: exact
     const int row = phys_row2(tr * T + rr, vg);
     gl[(size_t)row * vg.K2 + tc * T + cc] = make_float2((float)are[o] * inv, (float)aim[o] * inv);
   }
@@ -1102,11 +1104,21 @@ void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, fl
 void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write, float2* grid,
                  cudaStream_t st) {
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
+  if (!attr) { cudaFuncSetAttribute(k_grid<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
   size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(int);
-  k_grid<<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
-                               vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
+  k_grid<0><<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
+                                  cb.d_ncmax, vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
+  note_launches(1);
+}
+
+void launch_grid_count(const Cube& cb, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_grid<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
+  dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
+  size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(int);
+  k_grid<1><<<grd, 256, sm, st>>>(nullptr, nullptr, nullptr, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, nullptr,
+                                  cb.d_ncmax, vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
 }
 
