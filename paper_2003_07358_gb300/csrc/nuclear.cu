@@ -38,7 +38,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // sqrt(eps) s_max.)  Thread owns an LB x LB block of G; Lp = L rounded up to a
 // multiple of LB.  Output: FP64 partials [Q][nchunk_max][L][L].
 template <int LB>
-__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, const float* __restrict__ P,
+__global__ void __launch_bounds__(256, LB == 4 ? 1 : 3) k_gram(const float* __restrict__ xc, const float* __restrict__ P,
                                               const NucFacet* __restrict__ facets, const float* __restrict__ win,
                                               int n1, int n2, int L, int use_P, double* __restrict__ part,
                                               int nchunk_max) {
@@ -73,21 +73,59 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ xc, cons
 #pragma unroll
     for (int j = 0; j < LB; ++j) hi[i][j] = lo[i][j] = 0.f;
   const size_t N = (size_t)n1 * n2;
-  for (int s0 = p0; s0 < p1; s0 += kGramSub) {
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < kGramSub * Lp; idx += blockDim.x) {
-      int pix = idx % kGramSub, l = idx / kGramSub;
-      int p = s0 + pix;
+  // staging: thread -> pixel spix of the sub-chunk and channels sl0 + 4k; up to 16
+  // channels the next sub-chunk's values are loaded into registers while the current
+  // one is reduced
+  constexpr int NPT = LB == 2 ? 4 : 1;      // channels per thread (Lp <= 4 NPT when prefetching)
+  static_assert(kGramSub * 4 == 256, "256 threads stage 64 pixels x 4 channel lanes");
+  const int spix = threadIdx.x % kGramSub, sl0 = threadIdx.x / kGramSub;
+  float pre[NPT];
+  auto fetch = [&](int s0) {
+    const int p = s0 + spix;
+    const bool okp = p < p1;
+    int rr = 0, cc = 0;
+    float d = 0.f;
+    if (okp) {
+      rr = p / w;
+      cc = p - rr * w;
+      d = facet_weight(f, win, rr, cc);
+    }
+    const size_t xo = (size_t)(f.r0 + rr) * n2 + (f.c0 + cc);
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      const int l = sl0 + 4 * k;
       float val = 0.f;
-      if (p < p1 && l < L) {
-        int rr = p / w, cc = p - rr * w;
-        float d = facet_weight(f, win, rr, cc);
-        val = d * xc[l * N + (size_t)(f.r0 + rr) * n2 + (f.c0 + cc)];
+      if (okp && l < L) {
+        val = d * xc[l * N + xo];
         if (use_P) val += P[f.p_off + (size_t)l * Nq + p];
       }
-      z[pix][l] = val;
+      pre[k] = val;
+    }
+  };
+  constexpr bool PF = LB <= 2;         // prefetch (registers permitting)
+  if (PF) fetch(p0);
+  for (int s0 = p0; s0 < p1; s0 += kGramSub) {
+    if constexpr (PF) {
+#pragma unroll
+      for (int k = 0; k < NPT; ++k)
+        if (sl0 + 4 * k < Lp) z[spix][sl0 + 4 * k] = pre[k];
+    } else {
+#pragma unroll 4
+      for (int idx = threadIdx.x; idx < kGramSub * Lp; idx += blockDim.x) {
+        const int pix = idx % kGramSub, l = idx / kGramSub;
+        const int p = s0 + pix;
+        float val = 0.f;
+        if (p < p1 && l < L) {
+          const int rr = p / w, cc = p - rr * w;
+          const float d = facet_weight(f, win, rr, cc);
+          val = d * xc[l * N + (size_t)(f.r0 + rr) * n2 + (f.c0 + cc)];
+          if (use_P) val += P[f.p_off + (size_t)l * Nq + p];
+        }
+        z[pix][l] = val;
+      }
     }
     __syncthreads();
+    if (PF && s0 + kGramSub < p1) fetch(s0 + kGramSub);
     if (active) {
       for (int pix = g; pix < kGramSub; pix += G) {
         float a[LB], b[LB];
@@ -331,8 +369,10 @@ __global__ void __launch_bounds__(32) k_eig(const double* __restrict__ part, int
 
 // Pixel-driven update: each thread owns one pixel; for every facet covering it,
 // z = P_q + D_q x, P_q <- z M_q, A += zeta D_q P_q.  Row b of M_q^T is read as
-// float4 (one load per four FMAs, the same address across the warp), and A is
-// updated per facet so that only z lives in registers.
+// float4 (one load per four FMAs, the same address across the warp).  Up to 16
+// channels the A contributions of all covering facets are summed in shared memory
+// (one slot per thread and channel) and A is read and written once per pixel with all
+// of its loads in flight; above that, A is updated per facet.
 template <int LMAX>
 __global__ void __launch_bounds__(256) k_apply(const float* __restrict__ xc, float* __restrict__ P,
                                                const NucFacet* __restrict__ facets, const float* __restrict__ win,
@@ -346,6 +386,59 @@ __global__ void __launch_bounds__(256) k_apply(const float* __restrict__ xc, flo
   const size_t pix = (size_t)r * n2 + c;
   const int Lp = (L + 3) & ~3;
   const int ty = ty_of[r], tx = tx_of[c];
+  if constexpr (LMAX <= 16) {
+    __shared__ float sacc[LMAX][256];          // this thread's A contributions, per channel
+    float* acc = &sacc[0][threadIdx.x];
+#pragma unroll
+    for (int b = 0; b < LMAX; ++b) acc[b * 256] = 0.f;
+    for (int dy = 0; dy < 2; ++dy) {
+      const int qy = ty + dy;
+      if (qy >= Qy) break;
+      for (int dx = 0; dx < 2; ++dx) {
+        const int qx = tx + dx;
+        if (qx >= Qx) break;
+        const NucFacet f = facets[qy * Qx + qx];
+        if (r < f.r0 || r >= f.r1 || c < f.c0 || c >= f.c1) continue;
+        const int w = f.c1 - f.c0;
+        const int Nq = (f.r1 - f.r0) * w;
+        const int p = (r - f.r0) * w + (c - f.c0);
+        const float d = facet_weight(f, win, r - f.r0, c - f.c0);
+        float* Pq = P + f.p_off;
+        float z[LMAX];
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l) z[l] = (l < L) ? fmaf(d, xc[l * N + pix], Pq[(size_t)l * Nq + p]) : 0.f;
+        const float4* Mq = reinterpret_cast<const float4*>(Mt + (size_t)(qy * Qx + qx) * L * Lp);
+        const float zd = zeta * d;
+#pragma unroll 1
+        for (int b = 0; b < L; ++b) {
+          const float4* row = Mq + (size_t)b * (Lp / 4);
+          float s = 0.f;
+#pragma unroll
+          for (int a4 = 0; a4 < LMAX / 4; ++a4) {
+            if (4 * a4 < L) {
+              const float4 m = __ldg(row + a4);
+              s = fmaf(z[4 * a4], m.x, s);
+              s = fmaf(z[4 * a4 + 1], m.y, s);
+              s = fmaf(z[4 * a4 + 2], m.z, s);
+              s = fmaf(z[4 * a4 + 3], m.w, s);
+            }
+          }
+          Pq[(size_t)b * Nq + p] = s;
+          acc[b * 256] = fmaf(zd, s, acc[b * 256]);
+        }
+      }
+    }
+#pragma unroll
+    for (int b0 = 0; b0 < LMAX; b0 += 8) {
+      float a_old[8];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) a_old[b] = (b0 + b < L) ? A[(b0 + b) * N + pix] : 0.f;
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+        if (b0 + b < L) A[(b0 + b) * N + pix] = a_old[b] + acc[(b0 + b) * 256];
+    }
+    return;
+  }
   for (int dy = 0; dy < 2; ++dy) {
     int qy = ty + dy;
     if (qy >= Qy) break;
