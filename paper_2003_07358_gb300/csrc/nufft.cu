@@ -822,6 +822,8 @@ __global__ void k_l2ball_scale(const float2* __restrict__ d, const float* __rest
 // overflow, and the resolution is n_c m / 2^30 (about 2^-23 of m for the densest
 // tiles of the large workload, n_c ~ 100).
 
+constexpr int kGridThreads = 128;                // threads per gridding CTA
+
 // Source range [beg, end) of pass (dr, dc) for destination tile (tr, tc).
 __device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, int tr, int tc, int ntr, int ntc,
                                                 int& sr, int& sc, int& beg, int& end) {
@@ -867,14 +869,15 @@ __device__ __forceinline__ void grid_taps(int* are, int* aim, int TP, int lr, in
 // context): count the footprints covering each cell and store the tile's maximum in
 // ncmax[l][tile].
 template <int MODE>
-__global__ void __launch_bounds__(256, 4) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
+__global__ void __launch_bounds__(kGridThreads, 1024 / kGridThreads) k_grid(const float2* __restrict__ vals, const float* __restrict__ blk_scale,
                                               float2* __restrict__ v_write, const float2* __restrict__ uv,
                                               const uint8_t* __restrict__ blk, const int32_t* __restrict__ tile_off,
                                               const int64_t* __restrict__ vis_off, float2* __restrict__ grid,
                                               int* __restrict__ ncmax, VisGeom vg, int T, int ntr, int ntc, int B) {
   extern __shared__ __align__(16) int sacc_i[];
-  __shared__ float sred[8];
-  __shared__ int sredi[8];
+  constexpr int NW = kGridThreads / 32;
+  __shared__ float sred[NW];
+  __shared__ int sredi[NW];
   const int TP = T;                      // row stride, a multiple of 32: bank = column mod 32
   int* are = sacc_i;
   int* aim = are + T * TP;
@@ -908,7 +911,7 @@ __global__ void __launch_bounds__(256, 4) k_grid(const float2* __restrict__ vals
     __syncthreads();
     m = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) m = fmaxf(m, sred[w]);
+    for (int w = 0; w < NW; ++w) m = fmaxf(m, sred[w]);
     const int nc = ncmax[l * ntr * ntc + tau];
     if (m > 1e-30f && nc > 0) {
       // S = 2^e <= 2^30 / (n_c m'), m' = m (1 + 2^-10) covering the roundings of v s,
@@ -966,7 +969,7 @@ __global__ void __launch_bounds__(256, 4) k_grid(const float2* __restrict__ vals
     if ((threadIdx.x & 31) == 0) sredi[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 0; w < 8; ++w) mx = max(mx, sredi[w]);
+      for (int w = 0; w < NW; ++w) mx = max(mx, sredi[w]);
       ncmax[l * ntr * ntc + tau] = mx;
     }
     return;
@@ -1107,7 +1110,7 @@ void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, flo
   if (!attr) { cudaFuncSetAttribute(k_grid<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
   size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(int);
-  k_grid<0><<<grd, 256, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
+  k_grid<0><<<grd, kGridThreads, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
                                   cb.d_ncmax, vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
 }
@@ -1117,7 +1120,7 @@ void launch_grid_count(const Cube& cb, cudaStream_t st) {
   if (!attr) { cudaFuncSetAttribute(k_grid<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
   size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(int);
-  k_grid<1><<<grd, 256, sm, st>>>(nullptr, nullptr, nullptr, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, nullptr,
+  k_grid<1><<<grd, kGridThreads, sm, st>>>(nullptr, nullptr, nullptr, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, nullptr,
                                   cb.d_ncmax, vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
 }

@@ -382,6 +382,7 @@ struct SynFin2 {
   int64_t dirac_off;
   int n1, n2;
   float kappa;
+  int vec4;            // A, W, the Dirac block and n2 allow 16-byte accesses
 };
 
 // Level 1 of all bases: the tiles of basis b + 1 are staged (cp.async) while basis b
@@ -409,13 +410,25 @@ __global__ void __launch_bounds__(256, 3) k_synfin(SynFin2 s, float* __restrict_
   const int r = r0 + il;
   if (r >= s.n1) return;
   const size_t N = (size_t)s.n1 * s.n2;
-  const float* Wd = s.lv[0].W + (size_t)l * s.lv[0].I + s.dirac_off + (size_t)r * s.n2;
+  const size_t drow = (size_t)l * s.lv[0].I + s.dirac_off + (size_t)r * s.n2;
+  const float* Wd = s.lv[0].W + drow;
   float* Al = A + (size_t)l * N + (size_t)r * s.n2;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int c = c0 + jc0 + q;
-    if (c < s.n2) Al[c] = fmaf(s.kappa, acc[q] + Wd[c] * (1.f / 3.f), Al[c]);
+  const int c = c0 + jc0;
+  // four consecutive outputs: one 16-byte read-modify-write of A when the row and the
+  // Dirac block allow it
+  if (s.vec4 && c + 3 < s.n2) {
+    const float4 wd = *reinterpret_cast<const float4*>(Wd + c);
+    float4 a = *reinterpret_cast<const float4*>(Al + c);
+    a.x = fmaf(s.kappa, acc[0] + wd.x * (1.f / 3.f), a.x);
+    a.y = fmaf(s.kappa, acc[1] + wd.y * (1.f / 3.f), a.y);
+    a.z = fmaf(s.kappa, acc[2] + wd.z * (1.f / 3.f), a.z);
+    a.w = fmaf(s.kappa, acc[3] + wd.w * (1.f / 3.f), a.w);
+    *reinterpret_cast<float4*>(Al + c) = a;
+    return;
   }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (c + q < s.n2) Al[c + q] = fmaf(s.kappa, acc[q] + Wd[c + q] * (1.f / 3.f), Al[c + q]);
 }
 
 // ------------------------------------------------------------- launchers
@@ -532,6 +545,8 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
   fin.n1 = cb.n1;
   fin.n2 = cb.n2;
   fin.kappa = (float)cb.kappa;
+  fin.vec4 = (cb.n2 % 4 == 0 && S.dirac_off % 4 == 0 && S.I % 4 == 0 && ((uintptr_t)A % 16) == 0 &&
+              ((uintptr_t)W % 16) == 0) ? 1 : 0;
   dim3 g((cb.n2 + kT2 - 1) / kT2, (cb.n1 + kT2 - 1) / kT2, L);
   k_synfin<<<g, 256, 0, st>>>(fin, A);
   note_launches(1);
