@@ -417,7 +417,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
       bool down = lr + kTaps - 1 >= T, right = lc + kTaps - 1 >= T;
       int cls = down ? (right ? 2 : 1) : (right ? 3 : 0);
       key[i] = (tr * cb.ntile_c + tc) * 4 + cls;
-      res[i] = (uint8_t)(lc & 31);
+      res[i] = (uint8_t)((8 * lr + lc) & 31);
       cnt[key[i] + 1]++;
     }
     for (int k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
@@ -425,11 +425,14 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
     for (int k = 0; k <= nkeys; ++k) to[k] = cnt[k];
     order.assign(m, 0);
     for (int64_t i = 0; i < m; ++i) order[cnt[key[i]]++] = i;
-    // Within each (tile, class) bucket, deal the visibilities round-robin over the
-    // column of their first tap mod 32: 32 consecutive visibilities then have distinct
-    // residues, so the 32 lanes of a warp touch 32 different shared-memory banks at
-    // every tap in the gridder and 16 different bank pairs in the tile-staged
-    // degridder (row strides multiples of 32 and 16 cells).
+    // Within each (tile, class) bucket, deal the visibilities round-robin over
+    // (8 row + column) mod 32 of their first tap in the tile: 32 consecutive
+    // visibilities then have distinct residues, so the 32 lanes of a warp touch 32
+    // different shared-memory banks at every tap in the gridder and 16 different bank
+    // pairs per half-warp in the tile-staged degridder (row strides 8 mod 32 ints and
+    // 8 mod 16 float2).  Unlike the column alone, whose residues 26..31 cover one
+    // interior column where the others cover two, this key is close to uniform over a
+    // tile, so the rounds stay full.
     for (int k = 0; k < nkeys; ++k) {
       const int64_t b0 = to[k], b1 = to[k + 1];
       if (b1 - b0 <= 1) continue;

@@ -570,9 +570,10 @@ __global__ void __launch_bounds__(256) k_degrid_pdfb(const float2* __restrict__ 
 // TMA tensor copies (tile rows and halo rows of the digit-reversed grid, an mbarrier
 // with a bounded wait) except for the last tile column, whose halo wraps around the
 // grid edge and is staged with asynchronous 8-byte copies.  The staged row stride S
-// is a multiple of 16 float2 (the TMA box width), so a lane's bank pair is its column
-// mod 16, which the host's visibility order (first-tap column mod 32 distinct within
-// 32 consecutive visibilities) spreads over the warp.  MODE 0 stores
+// (the TMA box width) is 8 mod 16 float2, so a lane's bank pair is (8 row + column) mod
+// 16 of its first tap, which the host's visibility order ((8 row + column) mod 32
+// distinct within 32 consecutive visibilities) makes distinct within each half-warp
+// at every tap.  MODE 0 stores
 // u = G x_hat; MODE 1 is the PDFB data step of k_degrid_pdfb with its per-block
 // partial sums accumulated per warp in shared memory over the tile (fixed order)
 // and written once per CTA: partials[l][tile][2][B].
@@ -588,8 +589,8 @@ __device__ __forceinline__ void ff_accum(float2& acc, float x) {
   acc.y = __fadd_rn(acc.y, e);
 }
 
-// Staged row stride of the degridder (float2): T + 6 rounded up to 16.
-__host__ __device__ inline int degrid_stage_stride(int T) { return ((T + kTaps - 1 + 15) / 16) * 16; }
+// Staged row stride of the degridder (float2): the smallest S >= T + 6 with S = 8 mod 16.
+__host__ __device__ inline int degrid_stage_stride(int T) { return ((T + kTaps - 1 - 8 + 15) / 16) * 16 + 8; }
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__ grid, const float2* __restrict__ uv,
@@ -824,6 +825,12 @@ __global__ void k_l2ball_scale(const float2* __restrict__ d, const float* __rest
 
 constexpr int kGridThreads = 128;                // threads per gridding CTA
 
+// Row stride of the gridder's tile accumulators (ints): T + 8, which is 8 mod 32 for
+// T = 32 or 64, so the bank of cell (r, c) is (8 r + c) mod 32 and the host's
+// visibility order ((8 row + column) mod 32 of the first tap distinct within 32
+// consecutive visibilities) puts the 32 lanes of a warp on 32 banks at every tap.
+__host__ __device__ inline int grid_row_stride(int T) { return T + 8; }
+
 // Source range [beg, end) of pass (dr, dc) for destination tile (tr, tc).
 __device__ __forceinline__ void grid_pass_range(const int32_t* toff, int pass, int tr, int tc, int ntr, int ntc,
                                                 int& sr, int& sc, int& beg, int& end) {
@@ -878,7 +885,7 @@ __global__ void __launch_bounds__(kGridThreads, 1024 / kGridThreads) k_grid(cons
   constexpr int NW = kGridThreads / 32;
   __shared__ float sred[NW];
   __shared__ int sredi[NW];
-  const int TP = T;                      // row stride, a multiple of 32: bank = column mod 32
+  const int TP = grid_row_stride(T);     // = 8 mod 32: bank = (8 row + column) mod 32
   int* are = sacc_i;
   int* aim = are + T * TP;
   const int l = blockIdx.y;
@@ -1109,7 +1116,7 @@ void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, flo
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_grid<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
-  size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(int);
+  size_t sm = 2 * (size_t)cb.tile * grid_row_stride(cb.tile) * sizeof(int);
   k_grid<0><<<grd, kGridThreads, sm, st>>>(vals, blk_scale, v_write, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, grid,
                                   cb.d_ncmax, vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
@@ -1119,7 +1126,7 @@ void launch_grid_count(const Cube& cb, cudaStream_t st) {
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_grid<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
-  size_t sm = 2 * (size_t)cb.tile * cb.tile * sizeof(int);
+  size_t sm = 2 * (size_t)cb.tile * grid_row_stride(cb.tile) * sizeof(int);
   k_grid<1><<<grd, kGridThreads, sm, st>>>(nullptr, nullptr, nullptr, cb.d_uv, cb.d_blk, cb.d_tile_off, cb.d_vis_off, nullptr,
                                   cb.d_ncmax, vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, cb.B);
   note_launches(1);
