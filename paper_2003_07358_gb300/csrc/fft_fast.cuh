@@ -251,14 +251,120 @@ static void colA_adj_n(const Cube& cb, const float2* grid, float* out, const flo
   note_launches(1);
 }
 
+// Two-for-one transforms (K2 >= 2048, register row DFT).  Forward: step A packs two image
+// columns per complex column into the packed scratch, step B runs on its n2/2 columns, and
+// k_rowr_fwd_p unpacks each frequency pair (k, K1 - k) into two grid rows.  Adjoint:
+// k_rowr_adj_p transforms each pair of grid rows and packs the Hermitian parts of two
+// image columns per complex column, step B^H runs on n2/2 columns, and k_colA_adj_p
+// writes the real and imaginary parts of each output as two image columns.  Bytes per
+// channel and direction: 68N against 100N for the unpacked column-first order.
+bool fft_forward_packed(const Cube& cb) {
+  return cb.K2 >= 2048 && cb.K2 <= 8192 && cb.N1c >= 64 && cb.N1c <= 256 && cb.n2 % 64 == 0 &&
+         cb.n2 * 2 == cb.K2;
+}
+
+template <int N>
+static void colA_fwd_p_n(const Cube& cb, const float* x, float2* P, const float2* tw, int Kmax, cudaStream_t st) {
+  if constexpr (N >= 64 && N <= 256) {
+    static bool attr = false;
+    if (!attr) { cudaFuncSetAttribute(k_colA_fwd_p<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegCol<N>::SMEM); attr = true; }
+    dim3 grd((cb.n2 / 2 + 31) / 32, cb.N2c, cb.L);
+    k_colA_fwd_p<N><<<grd, 256, RegCol<N>::SMEM, st>>>(x, P, cb.d_scale_r, cb.d_scale_c, cb.n1, cb.n2, cb.K1, cb.N2c,
+                                                       tw, Kmax / N, Kmax / cb.K1);
+    note_launches(1);
+  }
+}
+
+template <int N>
+static void colB_p_n(const Cube& cb, float2* P, const float2* tw, int Kmax, cudaStream_t st) {
+  // step B over the n2/2 packed columns: row pitch n2/2, identity column map
+  Cube pc = cb;
+  pc.n2 = cb.n2 / 2;
+  pc.K2 = cb.n2 / 2;
+  colB_n<N>(pc, P, 0, tw, Kmax, st);
+}
+
+template <int N>
+static void rowr_p_n(const Cube& cb, float2* grid, const float2* P, const float2* tw, int Kmax, cudaStream_t st) {
+  if constexpr (N >= 2048) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_rowr_fwd_p<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegRow<N>::SMEM);
+      attr = true;
+    }
+    RowPack pk;
+    pk.P = P;
+    pk.hp = cb.n2 / 2;
+    pk.N1c = cb.N1c;
+    pk.lg1 = __builtin_ctz(cb.N1c);
+    pk.lg2 = __builtin_ctz(cb.N2c);
+    dim3 grd(cb.K1 / 2 + 1, cb.L);
+    k_rowr_fwd_p<N><<<grd, RegRow<N>::NT, RegRow<N>::SMEM, st>>>(grid, cb.K1, tw, Kmax / N, pk);
+    note_launches(1);
+  }
+}
+
 void launch_fft_forward_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float2* grid, cudaStream_t st) {
+  if (fft_forward_packed(cb) && ctx->s.pack) {
+    FHS_COL_SWITCH(cb.N1c, colA_fwd_p_n, cb, x, ctx->s.pack, ctx->d_tw, ctx->Kmax, st);
+    if (cb.N2c > 1) { FHS_COL_SWITCH(cb.N2c, colB_p_n, cb, ctx->s.pack, ctx->d_tw, ctx->Kmax, st); }
+    FHS_POW2_SWITCH(cb.K2, rowr_p_n, cb, grid, ctx->s.pack, ctx->d_tw, ctx->Kmax, st);
+    return;
+  }
   FHS_COL_SWITCH(cb.N1c, colA_fwd_n, cb, x, grid, ctx->d_tw, ctx->Kmax, st);
   if (cb.N2c > 1) { FHS_COL_SWITCH(cb.N2c, colB_n, cb, grid, 0, ctx->d_tw, ctx->Kmax, st); }
   FHS_POW2_SWITCH(cb.K2, row2_n, cb, grid, 0, ctx->d_tw, ctx->Kmax, st);
 }
 
+template <int N>
+static void rowr_adj_p_n(const Cube& cb, const float2* grid, float2* P, const float2* tw, int Kmax, cudaStream_t st) {
+  if constexpr (N >= 2048) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_rowr_adj_p<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegRowAdjP<N>::SMEM);
+      attr = true;
+    }
+    RowPack pk;
+    pk.P = P;
+    pk.hp = cb.n2 / 2;
+    pk.N1c = cb.N1c;
+    pk.lg1 = __builtin_ctz(cb.N1c);
+    pk.lg2 = __builtin_ctz(cb.N2c);
+    dim3 grd(cb.K1 / 2 + 1, cb.L);
+    k_rowr_adj_p<N><<<grd, RegRow<N>::NT, RegRowAdjP<N>::SMEM, st>>>(grid, P, cb.K1, tw, Kmax / N, pk);
+    note_launches(1);
+  }
+}
+
+template <int N>
+static void colB_pi_n(const Cube& cb, float2* P, const float2* tw, int Kmax, cudaStream_t st) {
+  Cube pc = cb;
+  pc.n2 = cb.n2 / 2;
+  pc.K2 = cb.n2 / 2;
+  colB_n<N>(pc, P, 1, tw, Kmax, st);
+}
+
+template <int N>
+static void colA_adj_p_n(const Cube& cb, const float2* P, float* out, const float* eta, bool acc, const float2* tw,
+                         int Kmax, cudaStream_t st) {
+  if constexpr (N >= 64 && N <= 256) {
+    static bool attr = false;
+    if (!attr) { cudaFuncSetAttribute(k_colA_adj_p<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegCol<N>::SMEM); attr = true; }
+    dim3 grd((cb.n2 / 2 + 31) / 32, cb.N2c, cb.L);
+    k_colA_adj_p<N><<<grd, 256, RegCol<N>::SMEM, st>>>(P, out, cb.d_scale_r, cb.d_scale_c, eta, acc ? 1 : 0, cb.n1,
+                                                       cb.n2, cb.K1, cb.N2c, tw, Kmax / N, Kmax / cb.K1);
+    note_launches(1);
+  }
+}
+
 void launch_fft_adjoint_fast(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta,
                              bool accumulate, cudaStream_t st) {
+  if (fft_forward_packed(cb) && ctx->s.pack && cb.n2 * 2 == cb.K2) {
+    FHS_POW2_SWITCH(cb.K2, rowr_adj_p_n, cb, grid, ctx->s.pack, ctx->d_tw, ctx->Kmax, st);
+    if (cb.N2c > 1) { FHS_COL_SWITCH(cb.N2c, colB_pi_n, cb, ctx->s.pack, ctx->d_tw, ctx->Kmax, st); }
+    FHS_COL_SWITCH(cb.N1c, colA_adj_p_n, cb, ctx->s.pack, out, eta, accumulate, ctx->d_tw, ctx->Kmax, st);
+    return;
+  }
   FHS_POW2_SWITCH(cb.K2, row2_n, cb, grid, 1, ctx->d_tw, ctx->Kmax, st);
   if (cb.N2c > 1) { FHS_COL_SWITCH(cb.N2c, colB_n, cb, grid, 1, ctx->d_tw, ctx->Kmax, st); }
   FHS_COL_SWITCH(cb.N1c, colA_adj_n, cb, grid, out, eta, accumulate, ctx->d_tw, ctx->Kmax, st);

@@ -83,6 +83,7 @@ struct Cube {
 
 struct Scratch {
   float2* grid = nullptr;    size_t grid_elems = 0;     // [L][K1][K2]
+  float2* pack = nullptr;                               // [L][K1][n2/2] packed column transform
   float* coef = nullptr;     size_t coef_elems = 0;     // [L][I]
   float* t0 = nullptr;       size_t t_elems = 0;        // SARA temporaries
   float* t1 = nullptr;
@@ -143,6 +144,7 @@ void launch_fft_forward(fhs_ctx* ctx, const Cube& cb, const float* x, float2* gr
 void launch_fft_adjoint(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta,
                         bool accumulate, cudaStream_t st);
 void launch_fft_forward_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float2* grid, cudaStream_t st);
+bool fft_forward_packed(const Cube& cb);
 void launch_fft_adjoint_fast(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta,
                              bool accumulate, cudaStream_t st);
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st);

@@ -532,6 +532,10 @@ void alloc_scratch(fhs_ctx* ctx) {
     ll1 = std::max(ll1, tot);
   }
   s.grid = dalloc<float2>(grid); s.grid_elems = grid;
+  size_t pack = 0;
+  for (const Cube& cb : ctx->cubes)
+    if (fft_forward_packed(cb)) pack = std::max(pack, (size_t)cb.L * cb.K1 * (cb.n2 / 2));
+  if (pack) s.pack = dalloc<float2>(pack);
   s.coef_elems = coef;          // allocated on first use of the plain path (ensure_coef)
   s.ll1 = dalloc<float>(ll1);
   s.t0 = dalloc<float>(tlx); s.t1 = dalloc<float>(tlx);
@@ -550,7 +554,7 @@ void alloc_scratch(fhs_ctx* ctx) {
 }
 
 void free_scratch(Scratch& s) {
-  void* ps[] = {s.grid, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.img2, s.vis, s.red, s.gram, s.nucM, s.blk_scale,
+  void* ps[] = {s.grid, s.pack, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.img2, s.vis, s.red, s.gram, s.nucM, s.blk_scale,
                 s.blk_out, s.ll1, s.stat};
   for (void* p : ps)
     if (p) cudaFree(p);
