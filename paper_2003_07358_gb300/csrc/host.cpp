@@ -623,14 +623,11 @@ void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
     const Cube& cb = ctx->cubes[c];
     const fhs_iterate& a = it[c];
     float* A = ctx->s.img;
-    const size_t nimg = (size_t)cb.L * cb.n1 * cb.n2;
     double* stat = ctx->s.stat + ctx->s.stat_stride * c;
     const int pp = primal_parts(cb);
-    FHS_CUDA(cudaMemsetAsync(A, 0, nimg * sizeof(float), st));
-    launch_nuclear(ctx, cb, a.Xcheck, a.state.P, a.state.theta_bar, A, false, nullptr, st);
-    check_launch("nuclear dual");
-    sara_dual(ctx, cb, a.Xcheck, a.state.W, a.state.theta, A);
-    // data fidelity: x_hat = F Z x, degrid + l2-ball duals, grid, adjoint
+    // data fidelity first: x_hat = F Z x, degrid + l2-ball duals, grid; its adjoint
+    // writes every pixel of A, and the nuclear and SARA duals then add to it (no
+    // clearing pass, no read of A in the adjoint)
     launch_fft_forward(ctx, cb, a.X, ctx->s.grid, st);
     int np;
     if (use_fast(ctx, cb)) {
@@ -648,8 +645,11 @@ void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
     timer_mark(ctx, FHS_TIMER_GRID, 2 * c);
     launch_grid(cb, ctx->s.vis, ctx->s.blk_scale, (float2*)a.state.v, ctx->s.grid, st);
     timer_mark(ctx, FHS_TIMER_GRID, 2 * c + 1);
-    launch_fft_adjoint(ctx, cb, ctx->s.grid, A, cb.d_eta, true, st);
+    launch_fft_adjoint(ctx, cb, ctx->s.grid, A, cb.d_eta, false, st);
     check_launch("adjoint");
+    launch_nuclear(ctx, cb, a.Xcheck, a.state.P, a.state.theta_bar, A, false, nullptr, st);
+    check_launch("nuclear dual");
+    sara_dual(ctx, cb, a.Xcheck, a.state.W, a.state.theta, A);
     launch_primal(cb, a.X, a.Xcheck, A, stat, pp, st);
     check_launch("primal");
   }
