@@ -205,28 +205,41 @@ static void colA_fwd_n(const Cube& cb, const float* x, float2* grid, const float
   note_launches(1);
 }
 
+// Step B over n2 columns of a grid with row pitch K2 (the packed transform: n2 = K2 = its
+// column count, identity column map).
+struct ColBDims {
+  int n2, K1, K2, N1c, L;
+};
+
+static ColBDims colb_dims(const Cube& cb) { return ColBDims{cb.n2, cb.K1, cb.K2, cb.N1c, cb.L}; }
+
 template <int N, bool INV>
-static void colB_r_n(const Cube& cb, float2* grid, const float2* tw, int Kmax, cudaStream_t st) {
+static void colB_r_n(const ColBDims& d, float2* grid, const float2* tw, int Kmax, cudaStream_t st) {
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_colB_r<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, RegCol<N>::SMEM); attr = true; }
-  dim3 grd((cb.n2 + 31) / 32, cb.N1c, cb.L);
-  k_colB_r<N, INV><<<grd, 256, RegCol<N>::SMEM, st>>>(grid, cb.n2, cb.K1, cb.K2, tw, Kmax / N);
+  dim3 grd((d.n2 + 31) / 32, d.N1c, d.L);
+  k_colB_r<N, INV><<<grd, 256, RegCol<N>::SMEM, st>>>(grid, d.n2, d.K1, d.K2, tw, Kmax / N);
   note_launches(1);
 }
 
 template <int N>
-static void colB_n(const Cube& cb, float2* grid, int inv, const float2* tw, int Kmax, cudaStream_t st) {
+static void colB_d(const ColBDims& d, float2* grid, int inv, const float2* tw, int Kmax, cudaStream_t st) {
   if constexpr (N >= 64 && N <= 256) {
-    if (inv) colB_r_n<N, true>(cb, grid, tw, Kmax, st);
-    else colB_r_n<N, false>(cb, grid, tw, Kmax, st);
+    if (inv) colB_r_n<N, true>(d, grid, tw, Kmax, st);
+    else colB_r_n<N, false>(d, grid, tw, Kmax, st);
     return;
   }
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_colB<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
   constexpr int W = ColCfg<N>::W;
-  dim3 grd((cb.n2 + W - 1) / W, cb.N1c, cb.L);
-  k_colB<N><<<grd, ColCfg<N>::NT, (size_t)N * W * sizeof(float2), st>>>(grid, cb.n2, cb.K1, cb.K2, inv, tw, Kmax / N);
+  dim3 grd((d.n2 + W - 1) / W, d.N1c, d.L);
+  k_colB<N><<<grd, ColCfg<N>::NT, (size_t)N * W * sizeof(float2), st>>>(grid, d.n2, d.K1, d.K2, inv, tw, Kmax / N);
   note_launches(1);
+}
+
+template <int N>
+static void colB_n(const Cube& cb, float2* grid, int inv, const float2* tw, int Kmax, cudaStream_t st) {
+  colB_d<N>(colb_dims(cb), grid, inv, tw, Kmax, st);
 }
 
 template <int N>
@@ -278,10 +291,7 @@ static void colA_fwd_p_n(const Cube& cb, const float* x, float2* P, const float2
 template <int N>
 static void colB_p_n(const Cube& cb, float2* P, const float2* tw, int Kmax, cudaStream_t st) {
   // step B over the n2/2 packed columns: row pitch n2/2, identity column map
-  Cube pc = cb;
-  pc.n2 = cb.n2 / 2;
-  pc.K2 = cb.n2 / 2;
-  colB_n<N>(pc, P, 0, tw, Kmax, st);
+  colB_d<N>(ColBDims{cb.n2 / 2, cb.K1, cb.n2 / 2, cb.N1c, cb.L}, P, 0, tw, Kmax, st);
 }
 
 template <int N>
@@ -338,10 +348,7 @@ static void rowr_adj_p_n(const Cube& cb, const float2* grid, float2* P, const fl
 
 template <int N>
 static void colB_pi_n(const Cube& cb, float2* P, const float2* tw, int Kmax, cudaStream_t st) {
-  Cube pc = cb;
-  pc.n2 = cb.n2 / 2;
-  pc.K2 = cb.n2 / 2;
-  colB_n<N>(pc, P, 1, tw, Kmax, st);
+  colB_d<N>(ColBDims{cb.n2 / 2, cb.K1, cb.n2 / 2, cb.N1c, cb.L}, P, 1, tw, Kmax, st);
 }
 
 template <int N>
