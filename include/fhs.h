@@ -126,7 +126,9 @@ typedef struct {
 /* ---------------------------------------------------------------- context */
 /* Create a context for `ncubes` sub-cubes.  Sorts the visibilities of every
  * channel by grid tile (host counting sort), builds the FFT, Kaiser-Bessel,
- * Daubechies and facet tables and allocates scratch.  `stream` is a
+ * Daubechies and facet tables, counts per grid tile the largest number of 7x7
+ * footprints covering one cell (one kernel launch; it fixes the gridder's
+ * fixed-point scale) and allocates scratch.  `stream` is a
  * cudaStream_t (NULL = legacy default stream).  Synchronising.
  * Errors: INVALID_ARG (shape, NULL pointer, non-finite parameter),
  * UNSUPPORTED (shape outside this build), OOM, CUDA.                       */
