@@ -304,7 +304,6 @@ static void rowr_p_n(const Cube& cb, float2* grid, const float2* P, const float2
     }
     RowPack pk;
     pk.P = P;
-    pk.hp = cb.n2 / 2;
     pk.N1c = cb.N1c;
     pk.lg1 = __builtin_ctz(cb.N1c);
     pk.lg2 = __builtin_ctz(cb.N2c);
@@ -336,7 +335,6 @@ static void rowr_adj_p_n(const Cube& cb, const float2* grid, float2* P, const fl
     }
     RowPack pk;
     pk.P = P;
-    pk.hp = cb.n2 / 2;
     pk.N1c = cb.N1c;
     pk.lg1 = __builtin_ctz(cb.N1c);
     pk.lg2 = __builtin_ctz(cb.N2c);

@@ -82,7 +82,6 @@ struct RegRow {
 // column transform's physical order, frequency k at ((k & (N1c - 1)) << lg2) | (k >> lg1).
 struct RowPack {
   const float2* P;
-  int hp;                 // n2 / 2
   int N1c, lg1, lg2;
 };
 
