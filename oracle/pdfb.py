@@ -1,11 +1,11 @@
 """Faceted HyperSARA PDFB iteration (Algorithm 2), reweighting (Algorithm 1),
 parameters and metrics, float64.
 
-Readings of the paper used here (each also listed in the design doc):
+Readings of the paper used here:
   * indicator iota_C is 0 on C and +inf outside (Eq. 3 states it inverted);
   * U_{c,l,b} = I: Euclidean projection onto the l2 balls, eta_l = 1 / ||Phi_l||_S^2;
   * the data dual uses Phi x_check^{(p)} = 2 Phi x^{(p)} - Phi x^{(p-1)} with
-    Phi x^{(-1)} := Phi x^{(0)} (Algorithm 2, lines computing x_hat and v);
+    Phi x^{(-1)} := Phi x^{(0)} (the x_hat and v updates of Algorithm 2);
   * P~_{c,q} = D_q P_{c,q} (Algorithm 2 writes P_c);
   * thresholds alpha_j = zeta^-1 mu_bar_q theta_bar_j paired with the singular
     values in descending order; alpha_i = kappa^-1 mu theta_i per wavelet row;
