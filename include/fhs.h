@@ -237,22 +237,29 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
  *
  * Same result as fhs_proj_l2ball_blocks, on plain arrays: for each segment s,
  * v[i] = (z[i] - y[i]) (1 - min(1, eps[s] / ||z_s - y_s||_2)) for
- * seg_off[s] <= i < seg_off[s+1].
- *  z, y, v_out : device, complex64 (interleaved float pairs), caller's order;
+ * seg_off[s] <= i < seg_off[s+1]; v_s = 0 whenever ||z_s - y_s|| <= eps[s],
+ * the zero-norm case included.  A segment whose norm is NaN or Inf gets
+ * v_s = NaN.
+ *  z, y, v_out : device, complex64 (interleaved float pairs), caller's order,
+ *                at least seg_off[nseg] elements each;
  *  seg_off     : host [nseg + 1], non-decreasing, seg_off[0] >= 0;
  *  nseg        : 1..64 (the size of the static scratch; larger -> INVALID_ARG);
  *  eps         : host [nseg], finite, >= 0;
  *  dnorm_out   : host [nseg] receives ||z_s - y_s||_2 in FP64, or NULL;
- *                when not NULL the call synchronises `stream`;
+ *                when not NULL the call synchronises `stream` (so it must be
+ *                NULL while that stream is being captured into a graph) and
+ *                returns NONFINITE if a norm is NaN or Inf;
  *  stream      : cudaStream_t (NULL = legacy default stream).
  * Never calls cudaMalloc, cudaFree or any allocating routine.  Its scratch is a
  * fixed 156 KB array in the library's device globals, held by every GPU that
  * loads the library until the process exits and shared by all calls on a
  * device: calls that overlap on the GPU race and must be serialised by the
  * caller.  The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress, device current); make that first call before any
- * stream capture begins.  Errors: INVALID_ARG, CUDA, NONFINITE; the message is
- * returned by fhs_noalloc_last_error (per host thread). */
+ * (cudaGetSymbolAddress, device current) and keeps it for the process; make
+ * that first call before any stream capture begins, and do not reset the
+ * device (cudaDeviceReset) afterwards.  Three kernel launches per call.
+ * Errors: INVALID_ARG, CUDA, NONFINITE; the message is returned by
+ * fhs_noalloc_last_error (per host thread). */
 fhs_status fhs_proj_l2ball_noalloc(const float* z, const float* y, const int64_t* seg_off, int32_t nseg,
                                    const double* eps, float* v_out, double* dnorm_out, void* stream);
 const char* fhs_noalloc_last_error(void);

@@ -1055,13 +1055,14 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
       const double* blk = st + 2 * pp;
       double dx2 = 0.0, x2 = 0.0;
       for (int k = 0; k < pp; ++k) { dx2 += st[2 * k]; x2 += st[2 * k + 1]; }
-      double r2 = 0.0, e2 = 0.0;
+      double r2 = 0.0, e2 = 0.0, d2 = 0.0;
       for (int k = 0; k < cb.L * cb.B; ++k) {
         r2 += blk[cb.L * cb.B + k] * blk[cb.L * cb.B + k];
+        d2 += blk[k] * blk[k];       // ||v + Phi x_check - y|| of the data duals
         e2 += cb.eps[k] * cb.eps[k];
       }
-      FHS_REQUIRE(std::isfinite(dx2) && std::isfinite(x2) && std::isfinite(r2), FHS_ERR_NONFINITE,
-                  "non-finite iteration statistics");
+      FHS_REQUIRE(std::isfinite(dx2) && std::isfinite(x2) && std::isfinite(r2) && std::isfinite(d2),
+                  FHS_ERR_NONFINITE, "non-finite iteration statistics");
       stats[c].xi = x2 > 0 ? sqrt(dx2 / x2) : INFINITY;
       stats[c].res_norm = sqrt(r2);
       stats[c].eps_norm = sqrt(e2);

@@ -20,8 +20,14 @@
 //  * calls whose kernels overlap on the GPU (e.g. on unordered streams) race
 //    on the scratch array: the caller must serialise them;
 //  * the first call on each device looks up the device address of the scratch
-//    array with cudaGetSymbolAddress (the device must be current); make that
-//    first call before any stream capture begins.
+//    array with cudaGetSymbolAddress (the device must be current) and keeps it
+//    for the life of the process; make that first call before any stream
+//    capture begins, and do not reset the device (cudaDeviceReset) after it;
+//  * a segment whose norm is NaN or Inf gets v = NaN (never a silent zero); the
+//    status reports FHS_ERR_NONFINITE only when the norms are requested, since
+//    only then does the call synchronise;
+//  * with dnorm_out != NULL the call synchronises the stream, which is not
+//    allowed while the stream is being captured: pass NULL there.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -34,16 +40,24 @@
 namespace fhs {
 
 constexpr int kNoAllocMaxSeg = 64;     // segments (data blocks) per call
-constexpr int kNoAllocParts = 304;     // partial sums per segment (2 CTAs per SM)
+constexpr int kNoAllocParts = 304;     // most partial sums per segment (the scratch row length)
 constexpr int kNoAllocMaxDevices = 64;
 
 // [seg][part] partial sums, then per segment {scale, ||z - y||}
 static __device__ __align__(256) double g_l2_scratch[kNoAllocMaxSeg * kNoAllocParts + 2 * kNoAllocMaxSeg];
 
-// Partial sums of ||z - y||^2 over [beg, end): one slot per CTA, CTAs without
-// elements write 0, so every slot of the segment is written.
+// Segment table passed by value (kernel parameter space, no device allocation).
+struct NaSegs {
+  int64_t off[kNoAllocMaxSeg + 1];
+  double eps[kNoAllocMaxSeg];
+};
+
+// Partial sums of ||z - y||^2 of segment blockIdx.y: one slot per CTA of the row,
+// CTAs without elements write 0, so every slot the total reads is written by this call.
 __global__ void __launch_bounds__(256) k_na_partials(const float2* __restrict__ z, const float2* __restrict__ y,
-                                                     double* __restrict__ scratch, int64_t beg, int64_t end, int seg) {
+                                                     double* __restrict__ scratch, const NaSegs segs) {
+  const int seg = blockIdx.y;
+  const int64_t beg = segs.off[seg], end = segs.off[seg + 1];
   double s = 0.0;
   for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -63,22 +77,28 @@ __global__ void __launch_bounds__(256) k_na_partials(const float2* __restrict__ 
   }
 }
 
-// Fixed-order sum of a segment's partials; scale = max(0, 1 - eps / ||z - y||).
-__global__ void k_na_segment_total(double* __restrict__ scratch, int seg, double eps) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One thread per segment: fixed-order sum of its `nparts` partials and the scale
+// 1 - eps / ||z - y|| (0 inside the ball, the zero-norm case included).  A non-finite
+// norm gives a NaN scale, so a NaN or Inf in z or y shows up as NaN in v instead of
+// a silent zero.
+__global__ void k_na_segment_total(double* __restrict__ scratch, int nseg, int nparts, const NaSegs segs) {
+  const int seg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= nseg) return;
   double t = 0.0;
-  for (int p = 0; p < kNoAllocParts; ++p) t += scratch[seg * kNoAllocParts + p];
-  double dn = sqrt(t);
+  for (int p = 0; p < nparts; ++p) t += scratch[seg * kNoAllocParts + p];
+  const double dn = sqrt(t), eps = segs.eps[seg];
   double* fin = scratch + kNoAllocMaxSeg * kNoAllocParts;
-  fin[2 * seg] = dn > eps ? 1.0 - eps / dn : 0.0;
+  fin[2 * seg] = !isfinite(dn) ? nan("") : (dn > eps ? 1.0 - eps / dn : 0.0);
   fin[2 * seg + 1] = dn;
 }
 
-// v = (z - y) * scale over the segment.
+// v = (z - y) * scale over segment blockIdx.y.
 __global__ void k_na_scale(const float2* __restrict__ z, const float2* __restrict__ y, float2* __restrict__ v,
-                           const double* __restrict__ scratch, int64_t beg, int64_t end, int seg) {
+                           const double* __restrict__ scratch, const NaSegs segs) {
+  const int seg = blockIdx.y;
+  const int64_t beg = segs.off[seg], end = segs.off[seg + 1];
   const double* fin = scratch + kNoAllocMaxSeg * kNoAllocParts;
-  float s = (float)fin[2 * seg];
+  const float s = (float)fin[2 * seg];
   for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
        i += (int64_t)gridDim.x * blockDim.x) {
     float2 a = z[i], b = y[i];
@@ -88,7 +108,8 @@ __global__ void k_na_scale(const float2* __restrict__ z, const float2* __restric
 
 namespace {
 std::mutex g_na_mu;
-double* g_na_ptr[kNoAllocMaxDevices] = {nullptr};
+double* g_na_ptr[kNoAllocMaxDevices] = {nullptr};   // device address of g_l2_scratch per device
+int g_na_parts[kNoAllocMaxDevices] = {0};           // partials per segment: 2 per SM, at most kNoAllocParts
 thread_local std::string g_na_err;
 }  // namespace
 
@@ -126,32 +147,48 @@ extern "C" fhs_status fhs_proj_l2ball_noalloc(const float* z, const float* y, co
     return FHS_ERR_CUDA;
   }
   double* scratch = nullptr;
+  int parts = 0;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (!g_na_ptr[dev]) {
-      // one-time set-up for this device: device address of the scratch array
+      // one-time set-up for this device: device address of the scratch array and
+      // the number of partial sums per segment (two CTAs per SM)
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_l2_scratch);
       if (e != cudaSuccess) {
         g_na_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
         return FHS_ERR_CUDA;
       }
+      int sms = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess || sms < 1) {
+        g_na_err = std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e);
+        return FHS_ERR_CUDA;
+      }
+      g_na_parts[dev] = std::min(kNoAllocParts, 2 * sms);
       g_na_ptr[dev] = (double*)p;
     }
     scratch = g_na_ptr[dev];
+    parts = g_na_parts[dev];
+  }
+  NaSegs segs;
+  int64_t longest = 0;
+  for (int s = 0; s <= nseg; ++s) segs.off[s] = seg_off[s];
+  for (int s = 0; s < nseg; ++s) {
+    segs.eps[s] = eps[s];
+    longest = std::max<int64_t>(longest, seg_off[s + 1] - seg_off[s]);
   }
   cudaStream_t st = (cudaStream_t)stream;
   const float2* z2 = (const float2*)z;
   const float2* y2 = (const float2*)y;
   float2* v2 = (float2*)v_out;
-  for (int s = 0; s < nseg; ++s) {
-    k_na_partials<<<kNoAllocParts, 256, 0, st>>>(z2, y2, scratch, seg_off[s], seg_off[s + 1], s);
-    k_na_segment_total<<<1, 32, 0, st>>>(scratch, s, eps[s]);
-    int64_t n = seg_off[s + 1] - seg_off[s];
-    unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(4 * 152, (n + 255) / 256));
-    k_na_scale<<<blocks, 256, 0, st>>>(z2, y2, v2, scratch, seg_off[s], seg_off[s + 1], s);
-    note_launches(3);
-  }
+  // three launches per call whatever the segment count: partials (segment = blockIdx.y),
+  // one thread per segment for the totals, then the scaling
+  k_na_partials<<<dim3(parts, nseg), 256, 0, st>>>(z2, y2, scratch, segs);
+  k_na_segment_total<<<1, kNoAllocMaxSeg, 0, st>>>(scratch, nseg, parts, segs);
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(2 * parts, (longest + 255) / 256));
+  k_na_scale<<<dim3(blocks, nseg), 256, 0, st>>>(z2, y2, v2, scratch, segs);
+  note_launches(3);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g_na_err = std::string("kernel launch: ") + cudaGetErrorString(e);

@@ -789,7 +789,8 @@ __global__ void __launch_bounds__(256) k_block_finalize(const double* __restrict
   if (threadIdx.x != 0) return;
   double dn = sqrt(s0s[0]);
   double e = eps ? eps[k] : 0.0;
-  if (scale) scale[k] = (float)(dn > e ? 1.0 - e / dn : 0.0);
+  // a NaN or Inf norm propagates as a NaN scale (v becomes NaN), never a silent zero
+  if (scale) scale[k] = (float)(!isfinite(dn) ? nan("") : (dn > e ? 1.0 - e / dn : 0.0));
   if (out) {
     out[k] = dn;
     out[L * B + k] = sqrt(s1s[0]);

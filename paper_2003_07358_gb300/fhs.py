@@ -120,20 +120,47 @@ def _ptr(t) -> int | None:
     return t.data_ptr()
 
 
+def _check_noalloc_args(z, y, seg_off: np.ndarray, eps: np.ndarray, v_out) -> None:
+    """Checks the C side cannot make (it has no lengths): raises ValueError before any
+    device work, so a wrong offset array can never read or write out of bounds."""
+    if seg_off.ndim != 1 or seg_off.size < 2:
+        raise ValueError("seg_off must be a 1-D array of nseg + 1 offsets")
+    if eps.shape != (seg_off.size - 1,):
+        raise ValueError(f"eps must have nseg = {seg_off.size - 1} entries, got shape {eps.shape}")
+    if seg_off[0] < 0 or np.any(np.diff(seg_off) < 0):
+        raise ValueError("seg_off must start at >= 0 and be non-decreasing")
+    need = int(seg_off[-1])
+    for name, t in (("z", z), ("y", y), ("v_out", v_out)):
+        if t is None or not hasattr(t, "dtype"):
+            raise ValueError(f"{name} must be a tensor")
+        if str(t.dtype) != "torch.complex64":
+            raise ValueError(f"{name} must be complex64, got {t.dtype}")
+        if t.numel() < need:
+            raise ValueError(f"{name} has {t.numel()} elements, the segments need {need}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if not (z.is_cuda and y.is_cuda and v_out.is_cuda):
+        raise ValueError("z, y and v_out must be CUDA tensors")
+    if not (z.device == y.device == v_out.device):
+        raise ValueError("z, y and v_out must be on the same device")
+
+
 def fhs_proj_l2ball_noalloc(z, y, seg_off, eps, v_out, want_norms: bool = True, stream=None):
     """Allocation-free l2-ball projection on plain arrays (no context): segment s
     of the caller's order gets v = (z - y)(1 - min(1, eps_s / ||z_s - y_s||)).
     For callers that may not allocate device memory; see include/fhs.h."""
-    import torch
-    lib = load()
     so = np.ascontiguousarray(seg_off, dtype=np.int64)
     ep = np.ascontiguousarray(eps, dtype=np.float64)
+    _check_noalloc_args(z, y, so, ep, v_out)
+    import torch
+    lib = load()
     out = np.zeros(so.size - 1, dtype=np.float64) if want_norms else None
-    st = stream if stream is not None else torch.cuda.current_stream()
+    st = stream if stream is not None else torch.cuda.current_stream(z.device)
     P = C.POINTER(C.c_double)
-    rc = lib.fhs_proj_l2ball_noalloc(_ptr(z), _ptr(y), so.ctypes.data_as(C.POINTER(C.c_int64)), so.size - 1,
-                                     ep.ctypes.data_as(P), _ptr(v_out), out.ctypes.data_as(P) if want_norms else None,
-                                     C.c_void_p(st.cuda_stream))
+    with torch.cuda.device(z.device):    # the C side works on the current device
+        rc = lib.fhs_proj_l2ball_noalloc(_ptr(z), _ptr(y), so.ctypes.data_as(C.POINTER(C.c_int64)), so.size - 1,
+                                         ep.ctypes.data_as(P), _ptr(v_out),
+                                         out.ctypes.data_as(P) if want_norms else None, C.c_void_p(st.cuda_stream))
     if rc != 0:
         raise FhsError(rc, lib.fhs_noalloc_last_error().decode())
     return out

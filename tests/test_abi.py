@@ -56,3 +56,24 @@ def test_binding_fails_loudly_without_library(tmp_path):
         fhs._lib = None
         fhs.load(str(tmp_path / "missing.so"))
     fhs._lib = None
+
+
+def test_noalloc_wrapper_rejects_bad_arguments_before_the_call():
+    """The allocation-free entry point has no length arguments, so its binding checks
+    the offsets, radii, dtypes and sizes on the host (ValueError, no device work)."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_2003_07358_gb300 import fhs
+    z = torch.zeros(10, dtype=torch.complex64)
+    v = torch.empty_like(z)
+    off = np.array([0, 4, 10])
+    with pytest.raises(ValueError, match="eps"):
+        fhs.fhs_proj_l2ball_noalloc(z, z, off, np.ones(3), v)
+    with pytest.raises(ValueError, match="non-decreasing"):
+        fhs.fhs_proj_l2ball_noalloc(z, z, np.array([0, 6, 4]), np.ones(2), v)
+    with pytest.raises(ValueError, match="complex64"):
+        fhs.fhs_proj_l2ball_noalloc(z.to(torch.complex128), z, off, np.ones(2), v)
+    with pytest.raises(ValueError, match="elements"):
+        fhs.fhs_proj_l2ball_noalloc(z, z, np.array([0, 4, 11]), np.ones(2), v)
+    with pytest.raises(ValueError, match="CUDA"):
+        fhs.fhs_proj_l2ball_noalloc(z, z, off, np.ones(2), v)

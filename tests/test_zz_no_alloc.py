@@ -66,3 +66,21 @@ def test_noalloc_rejects_too_many_segments():
     off = np.linspace(0, 100, 66).astype(np.int64)      # 65 segments > 64
     with pytest.raises(FhsError, match="nseg"):
         fhs_proj_l2ball_noalloc(z, z, off, np.ones(65), v)
+
+
+def test_noalloc_nonfinite_input_is_never_a_silent_zero():
+    """A NaN in z makes its segment's v NaN when the norms are not requested (the call
+    does not synchronise), and the call reports NONFINITE when they are."""
+    from paper_2003_07358_gb300.fhs import FhsError, fhs_proj_l2ball_noalloc
+    rng = np.random.default_rng(5)
+    z = torch.as_tensor((rng.standard_normal(300) + 1j * rng.standard_normal(300)).astype(np.complex64), device="cuda")
+    y = torch.zeros_like(z)
+    z[150] = complex(float("nan"), 0.0)
+    off = np.array([0, 100, 300], dtype=np.int64)
+    v = torch.empty_like(z)
+    fhs_proj_l2ball_noalloc(z, y, off, np.array([1.0, 1.0]), v, want_norms=False)
+    got = v.cpu().numpy()
+    assert np.all(np.isnan(got[100:300]))
+    assert np.all(np.isfinite(got[:100]))
+    with pytest.raises(FhsError, match="NONFINITE"):
+        fhs_proj_l2ball_noalloc(z, y, off, np.array([1.0, 1.0]), v)
