@@ -52,7 +52,7 @@ def jacobi_svd(A: np.ndarray, tol: float = 1e-15, max_sweeps: int = 60):
                     continue
                 rotated = True
                 zeta = (beta - alpha) / (2.0 * gamma)
-                t = np.sign(zeta) / (abs(zeta) + np.sqrt(1.0 + zeta * zeta)) if zeta != 0 else 1.0
+                t = np.sign(zeta) / (abs(zeta) + np.hypot(1.0, zeta)) if zeta != 0 else 1.0
                 c = 1.0 / np.sqrt(1.0 + t * t)
                 s = c * t
                 bp, bq = B[:, p].copy(), B[:, q].copy()
