@@ -171,3 +171,47 @@ def nuclear_facets(n1, n2, Qy, Qx, rho, kind):
             c0, c1, wx = fx[qx]
             out.append({"rows": (r0, r1), "cols": (c0, c1), "D": np.outer(wy, wx)})
     return out
+
+
+def sara_facet_analysis_local(x: np.ndarray, Qy: int, Qx: int, qy: int, qx: int):
+    """Psi_q^dagger S_q x computed from the facet input region alone (Section 2.4.2).
+
+    Same result and index order as ``sara_facet_analysis``, for images too large to
+    transform whole: S_q x is zero outside its input rectangle [s0, b0), so the
+    transform of the crop starting at a0 = s0 rounded down to a multiple of 2^LEVELS
+    (pixels of the crop before s0 set to zero) holds every owned coefficient; level-j
+    index k of the crop is global index k + a0 / 2^j, since the odd-phase decimation
+    c[k] = sum_t f[t] a[2k + 1 - t] commutes with shifts by even amounts at every level.
+    """
+    n1, n2 = x.shape[-2:]
+    step = 2 ** wv.LEVELS
+    (sy, by), (sx, bx) = sara_facet_input_1d(n1, Qy)[qy], sara_facet_input_1d(n2, Qx)[qx]
+    ay, ax = (sy // step) * step, (sx // step) * step
+    crop = np.array(x[..., ay:by, ax:bx], dtype=np.float64, copy=True)
+    crop[..., : sy - ay, :] = 0.0
+    crop[..., :, : sx - ax] = 0.0
+    cc = wv.sara_analysis(crop)
+    ctab, _ = wv.coefficient_map(by - ay, bx - ax)
+    gtab, _ = wv.coefficient_map(n1, n2)
+    parts, idx = [], []
+    for b in range(8):
+        F = 2 * (b + 1)
+        ry = owned_ranges_1d(n1, Qy, F)[qy]
+        rx = owned_ranges_1d(n2, Qx, F)[qx]
+        for j in range(1, wv.LEVELS + 1):
+            subs = [0, 1, 2] + ([3] if j == wv.LEVELS else [])
+            for s in subs:
+                goff, gr, gc = gtab[(b, j, s)]
+                coff, cr, ccol = ctab[(b, j, s)]
+                (a1, b1), (a2, b2) = ry[j], rx[j]
+                oy, ox = ay // 2 ** j, ax // 2 ** j
+                assert a1 >= oy and a2 >= ox and b1 - oy <= cr and b2 - ox <= ccol
+                rr, cl = np.meshgrid(np.arange(a1, b1), np.arange(a2, b2), indexing="ij")
+                idx.append((goff + rr * gc + cl).ravel())
+                parts.append(cc[..., coff + (rr - oy) * ccol + (cl - ox)].reshape(x.shape[:-2] + (-1,)))
+    tb1, tb2 = tile_bounds(n1, Qy), tile_bounds(n2, Qx)
+    goff, gr, gc = gtab[(8, 0, 0)]
+    rr, cl = np.meshgrid(np.arange(tb1[qy], tb1[qy + 1]), np.arange(tb2[qx], tb2[qx + 1]), indexing="ij")
+    idx.append((goff + rr * gc + cl).ravel())
+    parts.append((x[..., rr, cl] / 3.0).reshape(x.shape[:-2] + (-1,)))
+    return np.concatenate(idx), np.concatenate(parts, axis=-1)

@@ -1,0 +1,86 @@
+"""End-to-end parity of fhs_pdfb_iter with stored FP64 oracle runs (written by
+tests/golden/make_pdfb_runs.py, which runs only the oracle):
+
+* tiny workload (64 x 64, L = 4, Q = 1): 200 PDFB iterations, one weight update
+  (Algorithm 1, Eqs. 9-10), 200 more;
+* faceted workload (256 x 256, L = 20, 4 x 4 facets, sine overlap, 2 blocks): 200 PDFB
+  iterations (Algorithm 2).
+
+Bar: reconstruction SNR (Section 4.2) of every channel and its mean within 0.05 dB of
+the oracle's, X at the stored sampled pixels within 1e-3 (normwise), and the last
+iteration's xi and ||r|| within 1e-3.  Both sides use the oracle's parameters (eta, eps,
+mu, mu_bar, stored) and the same complex64 data."""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import fhs_synth as fs
+from oracle import nufft as nu
+from oracle import pdfb as pd
+
+from _fixtures import rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _context_and_data(rec):
+    from paper_2003_07358_gb300.fhs import Context, CubeParams
+    spec = fs.workload(rec["workload"], **rec["over"])
+    inp = fs.make_inputs(spec)
+    L = inp.x_true.shape[0]
+    y = np.zeros(inp.uv.shape[0], dtype=np.complex128)
+    off = 0
+    for l in range(L):
+        m = int(inp.M_lb[l].sum())
+        sl = slice(off, off + m)
+        y[sl] = nu.measure(inp.x_true[l], inp.uv[sl]) + rec["sigma"][l] * inp.noise[sl]
+        off += m
+    y = y.astype(np.complex64)
+    cp = CubeParams(n1=spec.n, n2=spec.n, L=L, Qy=spec.Q, Qx=spec.Q, overlap=spec.overlap, window=spec.window,
+                    M_lb=inp.M_lb, uv=inp.uv, eta=np.array(rec["eta"]), mu=rec["mu"],
+                    mu_bar=np.array(rec["mu_bar"]), eps=np.array(rec["eps"]), tau=rec["tau"], zeta=rec["zeta"],
+                    kappa=rec["kappa"])
+    return spec, inp, Context([cp]), y
+
+
+@pytest.mark.parametrize("fname", ["tiny_pdfb_schedule.json", "faceted_pdfb200.json"])
+def test_pdfb_schedule_matches_stored_oracle_run(fname):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    rec = _load(fname)
+    spec, inp, ctx, y = _context_and_data(rec)
+    L, n = inp.x_true.shape[0], spec.n
+    X = torch.zeros((L, n, n), device="cuda")
+    yi = torch.empty(y.size, dtype=torch.complex64, device="cuda")
+    ctx.fhs_vis_to_internal(0, torch.as_tensor(y, device="cuda"), yi)
+    st = ctx.new_state(0)
+    it = [{"X": X, "Xcheck": torch.zeros_like(X), "y": yi, "state": st}]
+    stats = None
+    for step in rec["schedule"]:
+        if step == "reweight":
+            ctx.fhs_reweight(0, X, st["theta"], st["theta_bar"])
+        else:
+            stats = ctx.fhs_pdfb_iter(it, step)
+    Xg = X.double().cpu().numpy()
+    snr = pd.snr_db(inp.x_true, Xg)
+    ref = np.array(rec["snr_db"])
+    assert np.max(np.abs(snr - ref)) <= 0.05, (snr, ref)
+    assert abs(snr.mean() - ref.mean()) <= 0.05
+    pix = np.array(rec["sample_pixels"])
+    got = np.stack([Xg[l].ravel()[pix[l]] for l in range(L)])
+    assert rel_err(got, np.array(rec["sample_values"])) < 1e-3
+    assert rel_err(np.linalg.norm(Xg.reshape(L, -1), axis=1), np.array(rec["x_norm"])) < 1e-4
+    assert stats[0]["xi"] == pytest.approx(rec["xi_last"], rel=1e-3, abs=1e-7)
+    assert stats[0]["res_norm"] == pytest.approx(rec["res_norm_last"], rel=1e-3)
+    ctx.close()

@@ -92,3 +92,17 @@ def test_step_size_condition():
             (r0, r1), (c0, c1), D = f["rows"], f["cols"], f["D"]
             s2[r0:r1, c0:c1] += D * D
         assert 0.33 * (s2.max() + 1.0 + 1.0) < 1.0
+
+
+@pytest.mark.parametrize("n1,n2,Qy,Qx", [(96, 96, 3, 3), (64, 80, 2, 3), (600, 600, 2, 2)])
+def test_facet_local_analysis_equals_masked_global(n1, n2, Qy, Qx):
+    """The crop-based facet analysis (for large images) gives exactly the owned
+    coefficients of the transform of the masked full image, in the same order."""
+    rng = np.random.default_rng(n1 * Qy + n2)
+    x = rng.standard_normal((2, n1, n2))
+    for qy in range(Qy):
+        for qx in range(Qx):
+            idx, ref = fc.sara_facet_analysis(x, Qy, Qx, qy, qx)
+            idx2, got = fc.sara_facet_analysis_local(x, Qy, Qx, qy, qx)
+            assert np.array_equal(idx, idx2)
+            assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
