@@ -24,6 +24,9 @@ CASES = {
     "tiny": dict(name="tiny"),
     "faceted": dict(name="faceted", L=6),
     "nonsquare_ragged": dict(name="faceted", n=128, L=3, Q=3, m_ratio=0.37, B=3),
+    # dense coverage (about 25 visibilities per grid cell at the centre): the gridder's
+    # dense-tile rounding path
+    "dense": dict(name="tiny", n=64, L=2, m_abs=40000),
 }
 
 
