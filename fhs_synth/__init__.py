@@ -92,6 +92,13 @@ WORKLOADS = {
                             n=4096, L=2, C=1, Q=16, overlap=0.1, m_ratio=0.5, B=8,
                             isnr_db=30.0, n_blobs=250, n_points=250, curvature=0.01,
                             seed=4000),
+    # the large workload's nuclear facets (256 + 25 pixels a side) and sub-cube channel
+    # count (16) on a 1024 x 1024 image: about 2 GB on the device, for profiler captures
+    # of the facet kernels
+    "facet_slice": CubeSpec("facet_slice: 1024x1024, L=16 (1 sub-cube), 4x4 facets of 281^2, M=0.5N, B=8",
+                            n=1024, L=16, C=1, Q=4, overlap=0.1, m_ratio=0.5, B=8,
+                            isnr_db=30.0, n_blobs=60, n_points=60, curvature=0.01,
+                            seed=4100),
 }
 
 

@@ -118,6 +118,10 @@ struct fhs_ctx {
   // CUDA graph of one PDFB iteration of every cube, replayed on gstream
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // second stream of an iteration: the facet Grams and eigen-solves of the nuclear duals
+  // run beside the data term (they read Xcheck and P only) and join before the update of A
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<const void*> graph_key;
   uint64_t graph_kernels = 0;
@@ -182,6 +186,17 @@ bool sara_fast_supported(const Cube& cb);
 // nuclear (nuclear.cu)
 void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P, const float* theta_bar,
                     float* A, bool weights_mode, float* theta_bar_out, cudaStream_t st);
+// the two halves of launch_nuclear: facet Grams + eigen-solves (reads Xcheck and P only),
+// then P <- Z M_q and A += zeta D_q P_q
+void launch_nuclear_gram_eig(fhs_ctx* ctx, const Cube& cb, const float* xcheck, const float* P,
+                             const float* theta_bar, bool weights_mode, float* theta_bar_out, cudaStream_t st);
+void launch_nuclear_apply(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P, float* A, cudaStream_t st);
+
+// error-free facet Gram on tcgen05 tensor cores (gram_tc.cu): FP64 partials in the
+// layout of k_gram; false when the cube's channel count is outside what it supports
+bool launch_gram_tc(const Cube& cb, const float* xcheck, const float* P, double* part, int nchunk_max,
+                    cudaStream_t st);
+unsigned read_gram_status(bool clear);
 
 // primal (primal.cu)
 void launch_primal(const Cube& cb, float* X, float* Xc, const float* A, double* partials, int nparts,

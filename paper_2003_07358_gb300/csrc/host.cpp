@@ -628,6 +628,13 @@ void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
     // data fidelity first: x_hat = F Z x, degrid + l2-ball duals, grid; its adjoint
     // writes every pixel of A, and the nuclear and SARA duals then add to it (no
     // clearing pass, no read of A in the adjoint)
+    // fork: the facet Grams and eigen-solves of the nuclear duals (they read Xcheck and P
+    // only) run on the second stream beside the data term
+    FHS_CUDA(cudaEventRecord(ctx->ev_fork, st));
+    FHS_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    launch_nuclear_gram_eig(ctx, cb, a.Xcheck, a.state.P, a.state.theta_bar, false, nullptr, ctx->aux);
+    check_launch("nuclear Gram");
+    FHS_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
     launch_fft_forward(ctx, cb, a.X, ctx->s.grid, st);
     int np;
     if (use_fast(ctx, cb)) {
@@ -647,7 +654,8 @@ void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
     timer_mark(ctx, FHS_TIMER_GRID, 2 * c + 1);
     launch_fft_adjoint(ctx, cb, ctx->s.grid, A, cb.d_eta, false, st);
     check_launch("adjoint");
-    launch_nuclear(ctx, cb, a.Xcheck, a.state.P, a.state.theta_bar, A, false, nullptr, st);
+    FHS_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));          // join
+    launch_nuclear_apply(ctx, cb, a.Xcheck, a.state.P, A, st);
     check_launch("nuclear dual");
     sara_dual(ctx, cb, a.Xcheck, a.state.W, a.state.theta, A);
     launch_primal(cb, a.X, a.Xcheck, A, stat, pp, st);
@@ -696,12 +704,19 @@ fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, 
     FHS_CUDA(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
     FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
     FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
+    FHS_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     FHS_CUDA(cudaStreamSynchronize(ctx->stream));
   } catch (const Fail& e) {
     g_create_err = e.msg;
     for (Cube& cb : ctx->cubes) free_cube(cb);
     free_scratch(ctx->s);
     if (ctx->d_tw) cudaFree(ctx->d_tw);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    for (cudaEvent_t e2 : {ctx->ev_in, ctx->ev_out, ctx->ev_fork, ctx->ev_join})
+      if (e2) cudaEventDestroy(e2);
     delete ctx;
     return e.st;
   }
@@ -717,6 +732,12 @@ fhs_status fhs_destroy(fhs_ctx* ctx) {
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   for (Cube& cb : ctx->cubes) free_cube(cb);
   free_scratch(ctx->s);

@@ -482,6 +482,12 @@ static int nchunk_max(const Cube& cb) { return (cb.max_facet_pix + kGramChunk - 
 
 void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P, const float* theta_bar, float* A,
                     bool weights_mode, float* theta_bar_out, cudaStream_t st) {
+  launch_nuclear_gram_eig(ctx, cb, xcheck, P, theta_bar, weights_mode, theta_bar_out, st);
+  if (!weights_mode) launch_nuclear_apply(ctx, cb, xcheck, P, A, st);
+}
+
+void launch_nuclear_gram_eig(fhs_ctx* ctx, const Cube& cb, const float* xcheck, const float* P,
+                             const float* theta_bar, bool weights_mode, float* theta_bar_out, cudaStream_t st) {
   const int L = cb.L;
   const int Q = cb.Qy * cb.Qx;
   const int nch = nchunk_max(cb);
@@ -489,10 +495,12 @@ void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P,
   int use_P = (P != nullptr && !weights_mode) ? 1 : 0;
   if (weights_mode)
     k_gram_f64<<<gg, 256, 0, st>>>(xcheck, cb.d_facets, cb.d_win64, cb.n1, cb.n2, L, ctx->s.gram, nch);
+  else if (ctx->path == FHS_PATH_FAST && launch_gram_tc(cb, xcheck, use_P ? P : nullptr, ctx->s.gram, nch, st))
+    ;   // tensor-core Gram (L <= 32)
   else if (L <= 4) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   else if (L <= 16) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
   else k_gram<4><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
-  note_launches(1);
+  if (weights_mode || ctx->path != FHS_PATH_FAST || L > 32) note_launches(1);
   size_t sm = (size_t)2 * L * (L + 1) * sizeof(double) + L * sizeof(double) + 2 * (L / 2 + 1) * sizeof(double) +
               (L + 2 * (L / 2 + 1)) * sizeof(int);
   static bool attr = false;
@@ -500,7 +508,10 @@ void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P,
   k_eig<<<Q, 32, sm, st>>>(ctx->s.gram, nch, cb.d_facets, L, theta_bar, cb.d_mubar, (float)(1.0 / cb.zeta),
                            ctx->s.nucM, theta_bar_out, weights_mode ? 1 : 0, 40);
   note_launches(1);
-  if (weights_mode) return;
+}
+
+void launch_nuclear_apply(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P, float* A, cudaStream_t st) {
+  const int L = cb.L;
   dim3 ga((cb.n2 + 31) / 32, (cb.n1 + 7) / 8);
   const int* tyo = cb.d_tile_of;
   const int* txo = cb.d_tile_of + cb.n1;

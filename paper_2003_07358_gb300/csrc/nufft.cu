@@ -1057,7 +1057,7 @@ unsigned read_device_status(bool clear) {
     const unsigned z = 0;
     cudaMemcpyToSymbol(g_dev_status, &z, sizeof(z));
   }
-  return v;
+  return v | (read_gram_status(clear) << 8);
 }
 
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st) {
