@@ -228,6 +228,43 @@ fhs_status fhs_kernel_timer_read(fhs_ctx* ctx, double* ms_total, int32_t* launch
  * fills the statistics of the last iteration. */
 fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fhs_iter_stats* stats);
 
+/* ------------------------------------------- Algorithm 1 with stopping rules */
+/* Stopping rules of Algorithm 2 (PDFB runs while p < p_min, or p < p_max and
+ * (xi > xi_pdfb or ||r|| > res_factor ||eps||); Section 4.1 uses res_factor = 1.01)
+ * and of Algorithm 1 (reweighting cycles run while t < t_max and
+ * xi_rw = ||X^(t+1) - X^(t)||_F / ||X^(t)||_F > xi_reweight). */
+enum { FHS_MAX_SOLVE_CYCLES = 32 };
+typedef struct {
+  int32_t p_min, p_max;        /* 1 <= p_min <= p_max                                */
+  double xi_pdfb;              /* >= 0                                               */
+  double res_factor;           /* >= 0                                               */
+  int32_t t_max;               /* 1 .. FHS_MAX_SOLVE_CYCLES                          */
+  double xi_reweight;          /* >= 0                                               */
+} fhs_solve_params;
+
+/* Outcome of fhs_solve for one cube (host). */
+typedef struct {
+  int32_t cycles;                                      /* reweighting cycles run       */
+  int32_t iterations;                                  /* PDFB iterations, all cycles  */
+  int32_t iterations_per_cycle[FHS_MAX_SOLVE_CYCLES];
+  double xi;                   /* last PDFB iteration's relative variation           */
+  double res_norm;             /* last PDFB iteration's ||r||                        */
+  double xi_reweight;          /* last cycle's relative variation of X               */
+  int32_t nonfinite;           /* 1 if a statistic was NaN or Inf (the loops stopped) */
+} fhs_solve_report;
+
+/* Algorithm 1 around Algorithm 2 on every cube, entirely on the device: per cube one
+ * CUDA graph with two nested WHILE nodes whose conditions are set by kernels that
+ * evaluate the stopping rules; no host round trip per iteration.  Cycle t: weights
+ * from X^(t) (Eqs. 9-10, into state.theta / state.theta_bar), X_check = X and
+ * u_prev = Phi X (Algorithm 2 restarts from X^(t)), PDFB iterations until the rule
+ * holds, then xi_rw.  The duals (W, P, v) carry over between cycles (warm start).
+ * it: host [ncubes] (as fhs_pdfb_iter); prm: host; report: host [ncubes], filled on
+ * return.  Synchronising.  Cubes run one after another.  Errors: INVALID_ARG,
+ * NONFINITE (a statistic was NaN or Inf; the report says where it stopped), TIMEOUT,
+ * CUDA.  The kernel timer (fhs_set_kernel_timer) records nothing inside fhs_solve. */
+fhs_status fhs_solve(fhs_ctx* ctx, const fhs_iterate* it, const fhs_solve_params* prm, fhs_solve_report* report);
+
 /* ------------------------------------------------- allocation-free variant */
 /* The paper has no counterpart of this entry point: it serves callers that may
  * not allocate device memory (a host application that owns all device memory

@@ -279,3 +279,34 @@ def build_problem(inp, isnr_db: float | None = None, power_iters: int = 100, see
                    uv=inp.uv, M_lb=M_lb, y=y, eps=eps, eta=1.0 / opn, mu=mu, mu_bar=mu_bar,
                    facets=facets)
     return prob, {"sigma": sig, "opnorm_sq": opn}
+
+
+# --------------------------------------------- Algorithms 1-2 with stopping rules
+def solve(prob: Problem, st: State, p_min: int, p_max: int, xi_pdfb: float, res_factor: float,
+          t_max: int, xi_reweight: float) -> list:
+    """Algorithm 1 around Algorithm 2, in place on st; returns one record per reweighting
+    cycle.  Cycle t: weights from X^(t) (Eqs. 9-10); Algorithm 2 restarted from X^(t)
+    (X_check^(0) = X^(0), Phi x^(-1) := Phi x^(0)), iterating while p < p_min, or
+    p < p_max and (xi > xi_pdfb or ||r|| > res_factor ||eps||), with xi and ||r|| those of
+    the last iteration; then xi_rw = ||X^(t+1) - X^(t)||_F / ||X^(t)||_F.  Cycles run while
+    t < t_max and xi_rw > xi_reweight (xi_rw = +inf before the first cycle and when
+    X^(t) = 0)."""
+    eps_norm = float(np.linalg.norm(prob.eps))
+    cycles = []
+    xi_rw = math.inf
+    t = 0
+    while t < t_max and xi_rw > xi_reweight:
+        st.theta, st.theta_bar = reweight(prob, st.X)
+        X_t = st.X.copy()
+        st.Xc = st.X.copy()
+        st.u_prev = measure_all(prob, st.X)
+        p, xi, res = 0, math.inf, math.inf
+        while p < p_min or (p < p_max and (xi > xi_pdfb or res > res_factor * eps_norm)):
+            out = pdfb_iteration(prob, st)
+            xi, res = out["xi"], float(np.linalg.norm(out["res"]))
+            p += 1
+        nt = np.linalg.norm(X_t)
+        xi_rw = float(np.linalg.norm(st.X - X_t) / nt) if nt > 0 else math.inf
+        cycles.append({"iterations": p, "xi": xi, "res_norm": res, "xi_rw": xi_rw})
+        t += 1
+    return cycles

@@ -19,6 +19,7 @@ constexpr int kLevels = 4;        // SARA decomposition levels
 constexpr int kMaxB = 16;         // data blocks per channel
 constexpr int kMaxL = 64;         // channels per cube
 constexpr int kMaxFilt = 16;      // longest Daubechies filter (db8)
+constexpr int kMaxSolveCycles = FHS_MAX_SOLVE_CYCLES;
 
 // ------------------------------------------------------------ device tables
 // Kaiser-Bessel weights: phi(f + 2.5 - j) = sum_d kb_poly[j][d] (2f - 1)^d, f in [0, 1).
@@ -128,6 +129,8 @@ struct fhs_ctx {
   // kernel timer: FHS_TIMER_* selection, one event pair per cube, whether an
   // iteration has recorded them since the selection
   int timer = FHS_TIMER_NONE;
+  bool timer_off = false;          // true while fhs_solve captures (no event nodes in its loops)
+  void* solve_dev = nullptr;       // [ncubes] device control states of fhs_solve
   std::vector<cudaEvent_t> tev;
   bool timer_armed = false;
 };
@@ -197,6 +200,17 @@ void launch_nuclear_apply(fhs_ctx* ctx, const Cube& cb, const float* xcheck, flo
 bool launch_gram_tc(const Cube& cb, const float* xcheck, const float* P, double* part, int nchunk_max,
                     cudaStream_t st);
 unsigned read_gram_status(bool clear);
+
+// device control of Algorithms 1-2 (solve.cu); the state is an opaque device struct
+size_t solve_state_bytes();
+void launch_solve_begin(void* sd, cudaStream_t st);
+void launch_solve_cycle_begin(const float* X, float* Xt, float* Xc, int64_t n, void* sd,
+                              cudaGraphConditionalHandle inner, cudaStream_t st);
+void launch_solve_pdfb_check(const double* stat, int pp, int LB, double eps_norm, const fhs_solve_params& prm,
+                             void* sd, cudaGraphConditionalHandle inner, cudaStream_t st);
+void launch_solve_cycle_check(const float* X, const float* Xt, int64_t n, double* part, const fhs_solve_params& prm,
+                              void* sd, cudaGraphConditionalHandle outer, cudaStream_t st);
+cudaError_t read_solve_state(const void* sd_dev, fhs_solve_report* rep, cudaStream_t st);
 
 // primal (primal.cu)
 void launch_primal(const Cube& cb, float* X, float* Xc, const float* A, double* partials, int nparts,

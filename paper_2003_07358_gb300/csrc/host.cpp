@@ -610,18 +610,16 @@ void adjoint_into(fhs_ctx* ctx, const Cube& cb, const float2* vals, const float*
 // (External record: inside a stream capture it becomes an event-record node of the
 // graph, so every replay records the event.)
 void timer_mark(fhs_ctx* ctx, int which, int k) {
-  if (ctx->timer != which) return;
+  if (ctx->timer != which || ctx->timer_off) return;
   FHS_CUDA(cudaEventRecordWithFlags(ctx->tev[k], ctx->stream, cudaEventRecordExternal));
 }
 
-// One iteration of Algorithm 2 on every cube, on ctx->stream; the primal partial
-// sums and the block norms of cube c land in its statistics region.
-void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
+// One iteration of Algorithm 2 on cube c, on ctx->stream; the primal partial sums and
+// the block norms land in the cube's statistics region.
+void pdfb_iteration_cube(fhs_ctx* ctx, int c, const fhs_iterate& a) {
   cudaStream_t st = ctx->stream;
-  const int nc = (int)ctx->cubes.size();
-  for (int c = 0; c < nc; ++c) {
+  {
     const Cube& cb = ctx->cubes[c];
-    const fhs_iterate& a = it[c];
     float* A = ctx->s.img;
     double* stat = ctx->s.stat + ctx->s.stat_stride * c;
     const int pp = primal_parts(cb);
@@ -661,6 +659,109 @@ void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
     launch_primal(cb, a.X, a.Xcheck, A, stat, pp, st);
     check_launch("primal");
   }
+}
+
+// One iteration of Algorithm 2 on every cube.
+void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
+  for (int c = 0; c < (int)ctx->cubes.size(); ++c) pdfb_iteration_cube(ctx, c, it[c]);
+}
+
+// Weights of Algorithm 1 (Eqs. 9-10) of cube c from x, on ctx->stream.
+void reweight_cube(fhs_ctx* ctx, const Cube& cb, const float* x, float* theta, float* theta_bar) {
+  cudaStream_t st = ctx->stream;
+  ensure_coef(ctx);
+  if (use_fast(ctx, cb)) {
+    launch_sara_fast(ctx, cb, x, nullptr, nullptr, nullptr, theta, true, st);
+  } else {
+    launch_sara_analysis(ctx, cb, x, ctx->s.coef, st);
+    launch_l21_weights(cb, ctx->s.coef, theta, st);
+  }
+  launch_nuclear(ctx, cb, x, nullptr, nullptr, nullptr, true, theta_bar, st);
+  check_launch("reweight");
+}
+
+// Adds a WHILE node at the current capture position of `st` and returns its body.
+cudaGraph_t capture_while_node(cudaStream_t st, cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  FHS_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  FHS_REQUIRE(cs == cudaStreamCaptureStatusActive, FHS_ERR_CUDA, "stream is not capturing");
+  cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+  prm.conditional.handle = h;
+  prm.conditional.type = cudaGraphCondTypeWhile;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  FHS_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+  FHS_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return prm.conditional.phGraph_out[0];
+}
+
+// The graph of Algorithm 1 around Algorithm 2 for cube c (see solve.cu):
+//   begin -> WHILE(outer) { weights; X_t = X, X_check = X; u_prev = Phi X;
+//                           WHILE(inner) { PDFB iteration; rule of Algorithm 2 };
+//                           xi_rw, rule of Algorithm 1 }
+// Captured on `cs` with ctx->stream redirected there.
+// Kernels captured in each part of the solve graph (for the launch counter).
+struct SolveCounts {
+  uint64_t top = 0, cycle = 0, iteration = 0;
+};
+
+cudaGraph_t build_solve_graph(fhs_ctx* ctx, int c, const fhs_iterate& a, const fhs_solve_params& prm, cudaStream_t cs,
+                              SolveCounts& cnt) {
+  const Cube& cb = ctx->cubes[c];
+  const int64_t n = (int64_t)cb.L * cb.n1 * cb.n2;
+  void* sd = (char*)ctx->solve_dev + (size_t)c * solve_state_bytes();
+  double eps2 = 0.0;
+  for (double e : cb.eps) eps2 += e * e;
+  const double eps_norm = sqrt(eps2);
+  const double* stat = ctx->s.stat + ctx->s.stat_stride * c;
+  float* Xt = ctx->s.img2;
+  cudaGraph_t top = nullptr;
+  FHS_CUDA(cudaGraphCreate(&top, 0));
+  try {
+    cudaGraphConditionalHandle h_out, h_in;
+    FHS_CUDA(cudaGraphConditionalHandleCreate(&h_out, top, 1, cudaGraphCondAssignDefault));
+    // top level: reset the control state, then the outer loop
+    FHS_CUDA(cudaStreamBeginCaptureToGraph(cs, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = cs;
+    uint64_t l0 = g_launches.load();
+    launch_solve_begin(sd, cs);
+    check_launch("solve begin");
+    cudaGraph_t body_out = capture_while_node(cs, h_out);
+    FHS_CUDA(cudaStreamEndCapture(cs, &top));
+    cnt.top = g_launches.load() - l0;
+    l0 = g_launches.load();
+    // outer body: one reweighting cycle
+    FHS_CUDA(cudaGraphConditionalHandleCreate(&h_in, body_out, 1, 0));
+    FHS_CUDA(cudaStreamBeginCaptureToGraph(cs, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    reweight_cube(ctx, cb, a.X, a.state.theta, a.state.theta_bar);
+    launch_solve_cycle_begin(a.X, Xt, a.Xcheck, n, sd, h_in, cs);
+    launch_measure(ctx, cb, a.X, (float2*)a.state.u_prev, cs);
+    check_launch("solve cycle begin");
+    cudaGraph_t body_in = capture_while_node(cs, h_in);
+    launch_solve_cycle_check(a.X, Xt, n, ctx->s.red, prm, sd, h_out, cs);
+    check_launch("solve cycle check");
+    FHS_CUDA(cudaStreamEndCapture(cs, &body_out));
+    cnt.cycle = g_launches.load() - l0;
+    l0 = g_launches.load();
+    // inner body: one PDFB iteration and the rule of Algorithm 2
+    FHS_CUDA(cudaStreamBeginCaptureToGraph(cs, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    pdfb_iteration_cube(ctx, c, a);
+    launch_solve_pdfb_check(stat, primal_parts(cb), cb.L * cb.B, eps_norm, prm, sd, h_in, cs);
+    check_launch("solve check");
+    FHS_CUDA(cudaStreamEndCapture(cs, &body_in));
+    cnt.iteration = g_launches.load() - l0;
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamCaptureStatus st_;
+    if (cudaStreamIsCapturing(cs, &st_) == cudaSuccess && st_ != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(cs, &g);
+    cudaGraphDestroy(top);
+    throw;
+  }
+  return top;
 }
 
 }  // namespace
@@ -928,18 +1029,63 @@ fhs_status fhs_proj_l2ball_blocks(fhs_ctx* ctx, int32_t cube, const float* z, co
 fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta, float* theta_bar) {
   return guarded(ctx, [&] {
     FHS_REQUIRE(x && theta && theta_bar, FHS_ERR_INVALID_ARG, "NULL array");
-    const Cube& cb = get_cube(ctx, cube);
-    cudaStream_t st = ctx->stream;
-    if (use_fast(ctx, cb)) {
-      ensure_coef(ctx);
-      launch_sara_fast(ctx, cb, x, nullptr, nullptr, nullptr, theta, true, st);
-    } else {
-      ensure_coef(ctx);
-      launch_sara_analysis(ctx, cb, x, ctx->s.coef, st);
-      launch_l21_weights(cb, ctx->s.coef, theta, st);
+    reweight_cube(ctx, get_cube(ctx, cube), x, theta, theta_bar);
+  });
+}
+
+fhs_status fhs_solve(fhs_ctx* ctx, const fhs_iterate* it, const fhs_solve_params* prm, fhs_solve_report* report) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(it && prm && report, FHS_ERR_INVALID_ARG, "NULL argument");
+    FHS_REQUIRE(prm->p_min >= 1 && prm->p_max >= prm->p_min && prm->t_max >= 1 &&
+                    prm->t_max <= FHS_MAX_SOLVE_CYCLES && std::isfinite(prm->xi_pdfb) && prm->xi_pdfb >= 0 &&
+                    std::isfinite(prm->res_factor) && prm->res_factor >= 0 && std::isfinite(prm->xi_reweight) &&
+                    prm->xi_reweight >= 0,
+                FHS_ERR_INVALID_ARG, "solve parameters out of range");
+    const int nc = (int)ctx->cubes.size();
+    for (int c = 0; c < nc; ++c) {
+      const fhs_iterate& a = it[c];
+      FHS_REQUIRE(a.X && a.Xcheck && a.y && a.state.W && a.state.theta && a.state.P && a.state.theta_bar &&
+                      a.state.v && a.state.u_prev,
+                  FHS_ERR_INVALID_ARG, "NULL array in fhs_iterate");
     }
-    launch_nuclear(ctx, cb, x, nullptr, nullptr, nullptr, true, theta_bar, st);
-    check_launch("reweight");
+    ensure_coef(ctx);   // no allocation may happen inside a capture
+    if (!ctx->solve_dev) ctx->solve_dev = dalloc<char>((size_t)nc * solve_state_bytes());
+    cudaStream_t user = ctx->stream;
+    // work queued on the caller's stream comes first
+    FHS_CUDA(cudaEventRecord(ctx->ev_in, user));
+    FHS_CUDA(cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0));
+    struct Restore {      // the caller's stream and the kernel timer, whatever happens
+      fhs_ctx* c;
+      cudaStream_t s;
+      ~Restore() { c->stream = s; c->timer_off = false; }
+    } restore{ctx, user};
+    ctx->timer_off = true;
+    bool nonfinite = false;
+    for (int c = 0; c < nc; ++c) {
+      const uint64_t l0 = g_launches.load();
+      SolveCounts cnt;
+      cudaGraph_t g = build_solve_graph(ctx, c, it[c], *prm, ctx->gstream, cnt);
+      ctx->stream = user;
+      g_launches.fetch_sub(g_launches.load() - l0);    // captured, not launched
+      cudaGraphExec_t ex = nullptr;
+      cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      FHS_CUDA(e);
+      e = cudaGraphLaunch(ex, ctx->gstream);
+      if (e == cudaSuccess)
+        e = read_solve_state((char*)ctx->solve_dev + (size_t)c * solve_state_bytes(), &report[c], ctx->gstream);
+      cudaGraphExecDestroy(ex);
+      FHS_CUDA(e);
+      // kernels run: the begin part once, the cycle body per cycle, the iteration body
+      // per PDFB iteration
+      note_launches((int)(cnt.top + cnt.cycle * (uint64_t)report[c].cycles +
+                          cnt.iteration * (uint64_t)report[c].iterations));
+      nonfinite = nonfinite || report[c].nonfinite;
+    }
+    FHS_CUDA(cudaEventRecord(ctx->ev_out, ctx->gstream));
+    FHS_CUDA(cudaStreamWaitEvent(user, ctx->ev_out, 0));
+    FHS_REQUIRE(read_device_status(true) == 0, FHS_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    FHS_REQUIRE(!nonfinite, FHS_ERR_NONFINITE, "a PDFB statistic was NaN or Inf; the solve stopped there");
   });
 }
 

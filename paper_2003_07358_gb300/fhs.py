@@ -26,8 +26,9 @@ SYMBOLS = [
     "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_prox_l21_sara_facets", "fhs_prox_nuclear_facets",
     "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
     "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path", "fhs_set_kernel_timer",
-    "fhs_kernel_timer_read",
+    "fhs_kernel_timer_read", "fhs_solve",
 ]
+MAX_SOLVE_CYCLES = 32
 FHS_PATH = {"fast": 0, "plain": 1}
 FHS_TIMER = {None: 0, "grid": 1, "degrid": 2}
 
@@ -63,6 +64,17 @@ class fhs_iterate(C.Structure):
 
 class fhs_iter_stats(C.Structure):
     _fields_ = [("xi", C.c_double), ("res_norm", C.c_double), ("eps_norm", C.c_double)]
+
+
+class fhs_solve_params(C.Structure):
+    _fields_ = [("p_min", C.c_int32), ("p_max", C.c_int32), ("xi_pdfb", C.c_double), ("res_factor", C.c_double),
+                ("t_max", C.c_int32), ("xi_reweight", C.c_double)]
+
+
+class fhs_solve_report(C.Structure):
+    _fields_ = [("cycles", C.c_int32), ("iterations", C.c_int32),
+                ("iterations_per_cycle", C.c_int32 * MAX_SOLVE_CYCLES), ("xi", C.c_double),
+                ("res_norm", C.c_double), ("xi_reweight", C.c_double), ("nonfinite", C.c_int32)]
 
 
 _lib = None
@@ -103,6 +115,7 @@ def load(path: str = LIB_PATH):
         "fhs_set_path": ([vp, i32], i32),
         "fhs_set_kernel_timer": ([vp, i32], i32),
         "fhs_kernel_timer_read": ([vp, C.POINTER(C.c_double), C.POINTER(i32)], i32),
+        "fhs_solve": ([vp, C.POINTER(fhs_iterate), C.POINTER(fhs_solve_params), C.POINTER(fhs_solve_report)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -293,18 +306,36 @@ class Context:
     def fhs_reweight(self, cube, x, theta, theta_bar):
         self._check(self.lib.fhs_reweight(self.h, cube, _ptr(x), _ptr(theta), _ptr(theta_bar)))
 
-    def fhs_pdfb_iter(self, iterates: list[dict], n_iter: int, want_stats: bool = True):
+    @staticmethod
+    def _iterates(iterates: list[dict]):
         arr = (fhs_iterate * len(iterates))()
         for a, it in zip(arr, iterates):
             a.X, a.Xcheck, a.y = _ptr(it["X"]), _ptr(it["Xcheck"]), _ptr(it["y"])
             s = it["state"]
             a.state.W, a.state.theta, a.state.P = _ptr(s["W"]), _ptr(s["theta"]), _ptr(s["P"])
             a.state.theta_bar, a.state.v, a.state.u_prev = _ptr(s["theta_bar"]), _ptr(s["v"]), _ptr(s["u_prev"])
+        return arr
+
+    def fhs_pdfb_iter(self, iterates: list[dict], n_iter: int, want_stats: bool = True):
+        arr = self._iterates(iterates)
         stats = (fhs_iter_stats * len(iterates))() if want_stats else None
         self._check(self.lib.fhs_pdfb_iter(self.h, arr, n_iter, stats))
         if not want_stats:
             return None
         return [{"xi": s.xi, "res_norm": s.res_norm, "eps_norm": s.eps_norm} for s in stats]
+
+    def fhs_solve(self, iterates: list[dict], p_min: int, p_max: int, xi_pdfb: float, res_factor: float,
+                  t_max: int, xi_reweight: float) -> list[dict]:
+        """Algorithm 1 around Algorithm 2 with their stopping rules, on the device (one
+        graph with nested WHILE nodes per cube); returns one report per cube."""
+        arr = self._iterates(iterates)
+        prm = fhs_solve_params(p_min, p_max, xi_pdfb, res_factor, t_max, xi_reweight)
+        reps = (fhs_solve_report * len(iterates))()
+        self._check(self.lib.fhs_solve(self.h, arr, C.byref(prm), reps))
+        return [{"cycles": r.cycles, "iterations": r.iterations,
+                 "iterations_per_cycle": list(r.iterations_per_cycle)[:r.cycles], "xi": r.xi,
+                 "res_norm": r.res_norm, "xi_reweight": r.xi_reweight, "nonfinite": bool(r.nonfinite)}
+                for r in reps]
 
     def fhs_set_params(self, cube, tau, zeta, kappa, eta, mu, mu_bar, eps):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (eta, mu_bar, eps)]

@@ -174,3 +174,31 @@ def test_pdfb_reaches_the_same_point_from_two_initialisations():
             pd.pdfb_iteration(prob, st)
         runs.append(st.X)
     assert np.linalg.norm(runs[0] - runs[1]) <= 1e-4 * np.linalg.norm(runs[0])
+
+
+def test_solve_follows_the_stopping_rules():
+    """Algorithm 1 around Algorithm 2: every cycle stops by its rule (p_max, or p >= p_min
+    with xi and ||r|| below their bounds), cycles stop at t_max or small xi_rw, and a cycle
+    with p_min = p_max = K is K plain iterations after a weight update and a restart."""
+    spec = fs.workload("tiny", n=16, L=2, m_abs=200)
+    inp = fs.make_inputs(spec)
+    prob, _ = pd.build_problem(inp, power_iters=60)
+    st = pd.initial_state(prob)
+    eps_norm = np.linalg.norm(prob.eps)
+    cyc = pd.solve(prob, st, p_min=5, p_max=150, xi_pdfb=5e-3, res_factor=1.01, t_max=4, xi_reweight=2e-2)
+    assert 1 <= len(cyc) <= 4
+    for c in cyc:
+        assert 5 <= c["iterations"] <= 150
+        if c["iterations"] < 150:
+            assert c["xi"] <= 5e-3 and c["res_norm"] <= 1.01 * eps_norm
+    assert len(cyc) == 4 or cyc[-1]["xi_rw"] <= 2e-2
+    assert all(c["xi_rw"] > 2e-2 for c in cyc[:-1])
+    assert cyc[0]["xi_rw"] == math.inf                 # X^(0) = 0
+    # fixed counts: one cycle of K iterations equals reweight + restart + K iterations
+    st1 = pd.initial_state(prob)
+    pd.solve(prob, st1, p_min=7, p_max=7, xi_pdfb=0.0, res_factor=1.0, t_max=1, xi_reweight=0.0)
+    st2 = pd.initial_state(prob)
+    st2.theta, st2.theta_bar = pd.reweight(prob, st2.X)
+    for _ in range(7):
+        pd.pdfb_iteration(prob, st2)
+    assert np.array_equal(st1.X, st2.X)
