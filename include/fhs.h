@@ -194,6 +194,20 @@ fhs_status fhs_proj_l2ball_blocks(fhs_ctx* ctx, int32_t cube, const float* z, co
  * (Eq. 10) and theta_bar_{q,j} = mu_bar_q / (s_j(D_q S~_q x) + mu_bar_q) (Eq. 9). */
 fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta, float* theta_bar);
 
+/* Parameters of a cube from its noise levels, computed on the device (Sections
+ * 2.3-2.4): ||Phi_l||_S^2 by the power method of fhs_opnorm_sq (power_iters,
+ * rel_tol), then eta_l = 1/||Phi_l||_S^2, eps_{l,b} = sqrt(sigma_l^2 (M_l + 2 sqrt(M_l))
+ * M_{l,b} / M_l) (Eq. 3), and with sigma_bar_l = sigma_l / ||Phi_l||_S and sigma_bar^2
+ * their mean square, mu = sigma_bar (m_chi(L) + s_chi(L)) (FHS sparsity heuristic) and
+ * mu_bar_q = sigma_bar sqrt(N~_q L / min(N~_q, L)) (low-rank heuristic); m_chi, s_chi
+ * are the mean and standard deviation of the chi distribution with L degrees of
+ * freedom.  The values replace the cube's eta, eps, mu and mu_bar (tau, zeta, kappa
+ * unchanged).  sigma: host [L], finite, >= 0.  Outputs (host, each may be NULL):
+ * eta [L], eps [L*B], mu [1], mu_bar [Qy*Qx].  Synchronising.
+ * Errors: INVALID_ARG, NONFINITE, UNSUPPORTED, CUDA. */
+fhs_status fhs_heuristic_params(fhs_ctx* ctx, int32_t cube, const double* sigma, int32_t power_iters, double rel_tol,
+                                double* eta_out, double* eps_out, double* mu_out, double* mu_bar_out);
+
 /* Replace the algorithm parameters of a cube (same meaning and host arrays as in
  * fhs_cube_desc: eta [L], mu_bar [Qy*Qx], eps [L*B]).  Lets a caller compute
  * eta = 1/||Phi_l||^2 with fhs_opnorm_sq and the noise-based heuristics

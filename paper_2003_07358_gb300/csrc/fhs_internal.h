@@ -73,6 +73,7 @@ struct Cube {
   float* d_scale_r = nullptr;                // [n1] deapodisation s_r
   float* d_scale_c = nullptr;                // [n2]
   double* d_eps = nullptr;                   // [L*B]
+  int64_t* d_M_lb = nullptr;                 // [L*B] visibilities per (channel, block)
   float* d_eta = nullptr;                    // [L]
   float* d_mubar = nullptr;                  // [Q]
   // TMA descriptors of the degridder's tile staging over the context's grid scratch,
@@ -211,6 +212,11 @@ void launch_solve_pdfb_check(const double* stat, int pp, int LB, double eps_norm
 void launch_solve_cycle_check(const float* X, const float* Xt, int64_t n, double* part, const fhs_solve_params& prm,
                               void* sd, cudaGraphConditionalHandle outer, cudaStream_t st);
 cudaError_t read_solve_state(const void* sd_dev, fhs_solve_report* rep, cudaStream_t st);
+
+// noise-based parameters (heuristics.cu): eta, eps, mu, mu_bar from sigma and ||Phi_l||^2
+// (device [L] each); out: device FP64 [eta L][eps L*B][mu][mu_bar Q]; updates the cube's
+// kernel-side parameter arrays
+void launch_heuristics(const Cube& cb, const double* sigma, const double* opn, double* out, cudaStream_t st);
 
 // primal (primal.cu)
 void launch_primal(const Cube& cb, float* X, float* Xc, const float* A, double* partials, int nparts,

@@ -473,6 +473,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
   cb.d_eps = dalloc<double>(cb.eps.size());
   cb.d_eta = dalloc<float>(d.L);
   cb.d_mubar = dalloc<float>(cb.mu_bar.size());
+  cb.d_M_lb = dalloc<int64_t>(cb.M_lb.size());
   std::vector<float> eta_f(cb.eta.begin(), cb.eta.end()), mub_f(cb.mu_bar.begin(), cb.mu_bar.end());
   upload(cb.d_uv, uv_int.data(), uv_int.size(), st);
   upload(cb.d_blk, blk_int.data(), blk_int.size(), st);
@@ -488,6 +489,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
   upload(cb.d_eps, cb.eps.data(), cb.eps.size(), st);
   upload(cb.d_eta, eta_f.data(), eta_f.size(), st);
   upload(cb.d_mubar, mub_f.data(), mub_f.size(), st);
+  upload(cb.d_M_lb, cb.M_lb.data(), cb.M_lb.size(), st);
   // per grid tile, the most footprints that cover one of its cells (fixes the
   // gridder's fixed-point scale; depends on the uv coverage only)
   cb.d_ncmax = dalloc<int>((size_t)d.L * cb.ntile_r * cb.ntile_c);
@@ -498,7 +500,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
 
 void free_cube(Cube& cb) {
   void* ps[] = {cb.d_uv, cb.d_blk, cb.d_perm, cb.d_vis_off, cb.d_tile_off, cb.d_facets, cb.d_win, cb.d_win64, cb.d_tile_of,
-                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar, cb.d_ncmax};
+                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar, cb.d_ncmax, cb.d_M_lb};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -766,6 +768,61 @@ cudaGraph_t build_solve_graph(fhs_ctx* ctx, int c, const fhs_iterate& a, const f
 
 }  // namespace
 
+namespace {
+// ||Phi_l||_S^2 of every channel of cube `cb` by the power method (Section 2.3.1
+// footnote); out: host [L].  Synchronising.
+void opnorm_sq(fhs_ctx* ctx, const Cube& cb, int32_t max_iter, double rel_tol, double* out) {
+  cudaStream_t st = ctx->stream;
+  const int L = cb.L;
+  const int64_t N = (int64_t)cb.n1 * cb.n2;
+  const int np = 64;
+  // deterministic pseudo-random start (xorshift64), unit norm per channel: a
+  // constant start is an even image and stays in the even eigenspace of the
+  // point-symmetric operator Re(Phi^dagger Phi)
+  std::vector<float> x0(N);
+  uint64_t state = 0x9E3779B97F4A7C15ull;
+  double nrm = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    state ^= state << 13; state ^= state >> 7; state ^= state << 17;
+    x0[i] = (float)((double)(state >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    nrm += (double)x0[i] * x0[i];
+  }
+  for (int64_t i = 0; i < N; ++i) x0[i] = (float)(x0[i] / sqrt(nrm));
+  for (int l = 0; l < L; ++l) upload(ctx->s.img2 + l * N, x0.data(), N, st);
+  std::vector<double> val(L, 0.0), inv(L);
+  std::vector<char> done(L, 0);
+  double* dinv = ctx->s.blk_out;   // L doubles of scratch
+  for (int it = 0; it < max_iter; ++it) {
+    launch_measure(ctx, cb, ctx->s.img2, ctx->s.vis, st);
+    adjoint_into(ctx, cb, ctx->s.vis, nullptr, nullptr, ctx->s.img, nullptr, false);
+    launch_sumsq(ctx->s.img, N, L, ctx->s.red, np, st);
+    check_launch("power method");
+    FHS_CUDA(cudaMemcpyAsync(ctx->s.red_host, ctx->s.red, (size_t)L * np * 2 * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    FHS_CUDA(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int l = 0; l < L; ++l) {
+      double s = 0.0;
+      for (int p = 0; p < np; ++p) s += ctx->s.red_host[2 * ((size_t)l * np + p)];
+      double nv = sqrt(s);
+      FHS_REQUIRE(std::isfinite(nv) && nv > 0, FHS_ERR_NONFINITE, "power method norm is not finite/positive");
+      if (!done[l] && val[l] > 0 && fabs(nv - val[l]) / nv < rel_tol) done[l] = 1;
+      val[l] = nv;
+      inv[l] = 1.0 / nv;
+      all = all && done[l];
+    }
+    if (all) break;
+    upload(dinv, inv.data(), L, st);
+    launch_scale_by_channel(ctx->s.img, N, L, dinv, st);
+    FHS_CUDA(cudaMemcpyAsync(ctx->s.img2, ctx->s.img, (size_t)L * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    check_launch("power method scale");
+  }
+  FHS_CUDA(cudaStreamSynchronize(st));
+  for (int l = 0; l < L; ++l) out[l] = val[l];
+}
+
+}  // namespace
+
 // ====================================================================== C ABI
 extern "C" {
 
@@ -917,54 +974,46 @@ fhs_status fhs_adjoint(fhs_ctx* ctx, int32_t cube, const float* v, float* x) {
 fhs_status fhs_opnorm_sq(fhs_ctx* ctx, int32_t cube, int32_t max_iter, double rel_tol, double* out) {
   return guarded(ctx, [&] {
     FHS_REQUIRE(out && max_iter >= 1, FHS_ERR_INVALID_ARG, "bad arguments");
-    const Cube& cb = get_cube(ctx, cube);
+    opnorm_sq(ctx, get_cube(ctx, cube), max_iter, rel_tol, out);
+  });
+}
+
+fhs_status fhs_heuristic_params(fhs_ctx* ctx, int32_t cube, const double* sigma, int32_t power_iters, double rel_tol,
+                                double* eta_out, double* eps_out, double* mu_out, double* mu_bar_out) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(sigma && power_iters >= 1 && std::isfinite(rel_tol) && rel_tol >= 0, FHS_ERR_INVALID_ARG,
+                "bad arguments");
+    FHS_REQUIRE(cube >= 0 && cube < (int32_t)ctx->cubes.size(), FHS_ERR_INVALID_ARG, "cube index out of range");
+    Cube& cb = ctx->cubes[cube];
+    const int L = cb.L, LB = cb.L * cb.B, Q = cb.Qy * cb.Qx;
+    for (int l = 0; l < L; ++l)
+      FHS_REQUIRE(std::isfinite(sigma[l]) && sigma[l] >= 0, FHS_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    std::vector<double> opn(L);
+    opnorm_sq(ctx, cb, power_iters, rel_tol, opn.data());
     cudaStream_t st = ctx->stream;
-    const int L = cb.L;
-    const int64_t N = (int64_t)cb.n1 * cb.n2;
-    const int np = 64;
-    // deterministic pseudo-random start (xorshift64), unit norm per channel: a
-    // constant start is an even image and stays in the even eigenspace of the
-    // point-symmetric operator Re(Phi^dagger Phi)
-    std::vector<float> x0(N);
-    uint64_t state = 0x9E3779B97F4A7C15ull;
-    double nrm = 0.0;
-    for (int64_t i = 0; i < N; ++i) {
-      state ^= state << 13; state ^= state >> 7; state ^= state << 17;
-      x0[i] = (float)((double)(state >> 11) * (1.0 / 9007199254740992.0) - 0.5);
-      nrm += (double)x0[i] * x0[i];
-    }
-    for (int64_t i = 0; i < N; ++i) x0[i] = (float)(x0[i] / sqrt(nrm));
-    for (int l = 0; l < L; ++l) upload(ctx->s.img2 + l * N, x0.data(), N, st);
-    std::vector<double> val(L, 0.0), inv(L);
-    std::vector<char> done(L, 0);
-    double* dinv = ctx->s.blk_out;   // L doubles of scratch
-    for (int it = 0; it < max_iter; ++it) {
-      launch_measure(ctx, cb, ctx->s.img2, ctx->s.vis, st);
-      adjoint_into(ctx, cb, ctx->s.vis, nullptr, nullptr, ctx->s.img, nullptr, false);
-      launch_sumsq(ctx->s.img, N, L, ctx->s.red, np, st);
-      check_launch("power method");
-      FHS_CUDA(cudaMemcpyAsync(ctx->s.red_host, ctx->s.red, (size_t)L * np * 2 * sizeof(double),
-                               cudaMemcpyDeviceToHost, st));
-      FHS_CUDA(cudaStreamSynchronize(st));
-      bool all = true;
-      for (int l = 0; l < L; ++l) {
-        double s = 0.0;
-        for (int p = 0; p < np; ++p) s += ctx->s.red_host[2 * ((size_t)l * np + p)];
-        double nv = sqrt(s);
-        FHS_REQUIRE(std::isfinite(nv) && nv > 0, FHS_ERR_NONFINITE, "power method norm is not finite/positive");
-        if (!done[l] && val[l] > 0 && fabs(nv - val[l]) / nv < rel_tol) done[l] = 1;
-        val[l] = nv;
-        inv[l] = 1.0 / nv;
-        all = all && done[l];
-      }
-      if (all) break;
-      upload(dinv, inv.data(), L, st);
-      launch_scale_by_channel(ctx->s.img, N, L, dinv, st);
-      FHS_CUDA(cudaMemcpyAsync(ctx->s.img2, ctx->s.img, (size_t)L * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-      check_launch("power method scale");
-    }
+    // inputs and outputs in the FP64 reduction scratch (>= 2 L + L B + 1 + Q doubles)
+    const size_t need = 2 * (size_t)L + LB + 1 + Q;
+    FHS_REQUIRE(need <= ctx->s.red_elems, FHS_ERR_UNSUPPORTED, "too many blocks or facets for the scratch");
+    double* d_in = ctx->s.red;
+    double* d_out = d_in + 2 * L;
+    std::vector<double> in(2 * L);
+    for (int l = 0; l < L; ++l) { in[l] = sigma[l]; in[L + l] = opn[l]; }
+    upload(d_in, in.data(), in.size(), st);
+    launch_heuristics(cb, d_in, d_in + L, d_out, st);
+    check_launch("heuristics");
+    std::vector<double> h(LB + L + 1 + Q);
+    FHS_CUDA(cudaMemcpyAsync(h.data(), d_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     FHS_CUDA(cudaStreamSynchronize(st));
-    for (int l = 0; l < L; ++l) out[l] = val[l];
+    for (double v : h) FHS_REQUIRE(std::isfinite(v), FHS_ERR_NONFINITE, "non-finite parameter");
+    // host mirrors (used for the statistics and by later fhs_set_params calls)
+    cb.eta.assign(h.begin(), h.begin() + L);
+    cb.eps.assign(h.begin() + L, h.begin() + L + LB);
+    cb.mu = h[L + LB];
+    cb.mu_bar.assign(h.begin() + L + LB + 1, h.end());
+    if (eta_out) std::copy(cb.eta.begin(), cb.eta.end(), eta_out);
+    if (eps_out) std::copy(cb.eps.begin(), cb.eps.end(), eps_out);
+    if (mu_out) *mu_out = cb.mu;
+    if (mu_bar_out) std::copy(cb.mu_bar.begin(), cb.mu_bar.end(), mu_bar_out);
   });
 }
 

@@ -26,7 +26,7 @@ SYMBOLS = [
     "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_prox_l21_sara_facets", "fhs_prox_nuclear_facets",
     "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
     "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path", "fhs_set_kernel_timer",
-    "fhs_kernel_timer_read", "fhs_solve",
+    "fhs_kernel_timer_read", "fhs_solve", "fhs_heuristic_params",
 ]
 MAX_SOLVE_CYCLES = 32
 FHS_PATH = {"fast": 0, "plain": 1}
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         "fhs_set_kernel_timer": ([vp, i32], i32),
         "fhs_kernel_timer_read": ([vp, C.POINTER(C.c_double), C.POINTER(i32)], i32),
         "fhs_solve": ([vp, C.POINTER(fhs_iterate), C.POINTER(fhs_solve_params), C.POINTER(fhs_solve_report)], i32),
+        "fhs_heuristic_params": ([vp, i32, dp, i32, C.c_double, dp, dp, dp, dp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -336,6 +337,21 @@ class Context:
                  "iterations_per_cycle": list(r.iterations_per_cycle)[:r.cycles], "xi": r.xi,
                  "res_norm": r.res_norm, "xi_reweight": r.xi_reweight, "nonfinite": bool(r.nonfinite)}
                 for r in reps]
+
+    def fhs_heuristic_params(self, cube, sigma, power_iters=100, rel_tol=1e-4) -> dict:
+        """eta, eps, mu, mu_bar of a cube from its noise levels sigma [L], computed on the
+        device (power method and the noise-based heuristics) and installed in the context."""
+        cp = self.cubes[cube]
+        L, B, Q = cp.L, int(np.asarray(cp.M_lb).shape[1]), cp.Qy * cp.Qx
+        sig = np.ascontiguousarray(sigma, dtype=np.float64)
+        if sig.shape != (L,):
+            raise ValueError(f"sigma must have {L} entries")
+        eta, eps, mu, mub = np.zeros(L), np.zeros(L * B), np.zeros(1), np.zeros(Q)
+        P = C.POINTER(C.c_double)
+        self._check(self.lib.fhs_heuristic_params(self.h, cube, sig.ctypes.data_as(P), power_iters, rel_tol,
+                                                  eta.ctypes.data_as(P), eps.ctypes.data_as(P),
+                                                  mu.ctypes.data_as(P), mub.ctypes.data_as(P)))
+        return {"eta": eta, "eps": eps.reshape(L, B), "mu": float(mu[0]), "mu_bar": mub}
 
     def fhs_set_params(self, cube, tau, zeta, kappa, eta, mu, mu_bar, eps):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (eta, mu_bar, eps)]
