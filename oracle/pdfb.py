@@ -28,13 +28,17 @@ from . import wavelets as wv
 
 # ------------------------------------------------------------------ parameters
 def op_norm_sq(uv: np.ndarray, n1: int, n2: int, x0: np.ndarray, max_iter: int = 100,
-               rel_tol: float = 1e-4) -> float:
+               rel_tol: float = 1e-4, U: np.ndarray | None = None) -> float:
     """||Phi||_S^2 on real images by the power method on Re(Phi^dagger Phi)
-    (footnote of Section 2.3.1: relative variation below 1e-4, at most 100 iterations)."""
+    (footnote of Section 2.3.1: relative variation below 1e-4, at most 100 iterations);
+    with a preconditioner, ||U^1/2 Phi||_S^2 from Re(Phi^dagger U Phi) (Section 3.2)."""
     x = x0 / np.linalg.norm(x0)
     val = 0.0
     for _ in range(max_iter):
-        y = nu.adjoint(nu.measure(x, uv), uv, n1, n2).real
+        m = nu.measure(x, uv)
+        if U is not None:
+            m = U * m
+        y = nu.adjoint(m, uv, n1, n2).real
         new = np.linalg.norm(y)
         x = y / new
         if val > 0 and abs(new - val) / new < rel_tol:
@@ -57,6 +61,20 @@ def l2_radii(sigma: float, M_b) -> np.ndarray:
     M = M_b.sum()
     e2 = sigma ** 2 * (M + 2.0 * math.sqrt(M))
     return np.sqrt(e2 * M_b / M)
+
+
+def inverse_density(uv: np.ndarray, n1: int, n2: int) -> np.ndarray:
+    """U of one channel (Section 3.2): the inverse of the sampling density near each
+    acquired Fourier mode, read as 1 / (number of the channel's visibilities whose
+    nearest cell of the 2n1 x 2n2 oversampled grid, round(omega K / 2 pi) mod K, is the
+    visibility's own)."""
+    uv = np.asarray(uv, dtype=np.float64)
+    K1, K2 = 2 * n1, 2 * n2
+    r = np.floor(uv[:, 1] * K1 / (2.0 * np.pi) + 0.5).astype(np.int64) % K1
+    c = np.floor(uv[:, 0] * K2 / (2.0 * np.pi) + 0.5).astype(np.int64) % K2
+    cell = r * K2 + c
+    _, inv, counts = np.unique(cell, return_inverse=True, return_counts=True)
+    return 1.0 / counts[inv]
 
 
 def chi_mean_std(k: int):
@@ -100,6 +118,8 @@ class Problem:
     zeta: float = 1.0
     kappa: float = 1.0
     facets: list = field(default_factory=list)
+    U: np.ndarray | None = None     # [sum M] diagonal preconditioner (None: U = I)
+    n_sub: int = 20                 # forward-backward sub-iterations of the U-projection
 
     def __post_init__(self):
         if not self.facets:
@@ -191,7 +211,10 @@ def data_step(prob: Problem, X: np.ndarray, v: np.ndarray, u_prev: np.ndarray):
     res = np.zeros(prob.M_lb.shape)
     for (l, b, sl) in prob.vis_slices():
         phixc = 2.0 * u[sl] - u_prev[sl]
-        vn[sl] = px.dual_l2ball(v[sl], phixc, prob.y[sl], prob.eps[l, b])
+        if prob.U is None:
+            vn[sl] = px.dual_l2ball(v[sl], phixc, prob.y[sl], prob.eps[l, b])
+        else:
+            vn[sl] = px.dual_l2ball_precond(v[sl], phixc, prob.y[sl], prob.eps[l, b], prob.U[sl], prob.n_sub)
         res[l, b] = np.linalg.norm(prob.y[sl] - u[sl])
     A = np.zeros_like(X)
     for l, sl in enumerate(prob.channel_slices()):
@@ -310,3 +333,18 @@ def solve(prob: Problem, st: State, p_min: int, p_max: int, xi_pdfb: float, res_
         cycles.append({"iterations": p, "xi": xi, "res_norm": res, "xi_rw": xi_rw})
         t += 1
     return cycles
+
+
+def precondition(prob: Problem, n_sub: int = 20, power_iters: int = 100, seed: int = 7) -> Problem:
+    """The preconditioned variant of Section 3.2 on prob (in place): U_{l,b} = inverse
+    sampling density of every channel, n_sub forward-backward sub-iterations for the
+    U-metric projections, and eta_l = 1 / ||U_l^1/2 Phi_l||_S^2."""
+    rng = np.random.default_rng(seed)
+    U = np.zeros(prob.uv.shape[0])
+    eta = np.zeros(prob.L)
+    for l, sl in enumerate(prob.channel_slices()):
+        U[sl] = inverse_density(prob.uv[sl], prob.n1, prob.n2)
+        eta[l] = 1.0 / op_norm_sq(prob.uv[sl], prob.n1, prob.n2, rng.standard_normal((prob.n1, prob.n2)),
+                                  max_iter=power_iters, U=U[sl])
+    prob.U, prob.n_sub, prob.eta = U, n_sub, eta
+    return prob

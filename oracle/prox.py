@@ -97,3 +97,24 @@ def dual_l2ball(v: np.ndarray, phix: np.ndarray, y: np.ndarray, eps: float) -> n
     """Algorithm 2 data dual with U = I: v <- (I - P_B(y, eps))(v + Phi x_check)."""
     z = v + phix
     return z - proj_l2ball(z, y, eps)
+
+
+def proj_l2ball_metric(z: np.ndarray, y: np.ndarray, eps: float, U: np.ndarray, n_sub: int) -> np.ndarray:
+    """prox^U of the indicator of B(y, eps) (Eq. prox_definition with a diagonal metric
+    U > 0), approximated by n_sub forward-backward steps on 1/2 (x - z)^H U (x - z) over
+    the ball (Section 3.2: sub-iterations of Euclidean projections): start from the
+    Euclidean projection P_B(z), then x <- P_B(x - gamma U (x - z)), gamma = 1 / max U."""
+    U = np.asarray(U, dtype=np.float64)
+    gamma = 1.0 / U.max()
+    x = proj_l2ball(z, y, eps)
+    for _ in range(n_sub):
+        x = proj_l2ball(x - gamma * U * (x - z), y, eps)
+    return x
+
+
+def dual_l2ball_precond(v: np.ndarray, phix: np.ndarray, y: np.ndarray, eps: float, U: np.ndarray,
+                        n_sub: int) -> np.ndarray:
+    """Algorithm 2 data dual with a diagonal preconditioner U:
+    v <- U (I - prox^U_B(y, eps))(U^-1 v + Phi x_check)."""
+    z = v / U + phix
+    return U * (z - proj_l2ball_metric(z, y, eps, U, n_sub))

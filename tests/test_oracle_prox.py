@@ -91,3 +91,57 @@ def test_weighted_nuclear_prox_rank_one_and_lapack():
     X0 = Z - P0
     d = px.dual_nuclear(P0, X0, alpha)
     assert np.allclose(d, (Uu * np.minimum(s, alpha)) @ Vt, atol=1e-12)
+
+
+def _metric_projection_closed_form(z, y, eps, U):
+    """argmin_{||x - y|| <= eps} (x - z)^H U (x - z): x(lam) = (U z + lam y) / (U + lam)
+    (stationarity with a multiplier lam >= 0), lam by bisection on ||x(lam) - y|| = eps."""
+    if np.linalg.norm(z - y) <= eps:
+        return z.copy()
+    lo, hi = 0.0, 1.0
+    f = lambda lam: np.linalg.norm((U * z + lam * y) / (U + lam) - y) - eps
+    while f(hi) > 0:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if f(mid) > 0 else (lo, mid)
+    lam = 0.5 * (lo + hi)
+    return (U * z + lam * y) / (U + lam)
+
+
+def test_metric_projection_reduces_and_converges():
+    rng = np.random.default_rng(11)
+    m = 300
+    y = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    z = y + 3.0 * (rng.standard_normal(m) + 1j * rng.standard_normal(m))
+    eps = 10.0
+    # U = I: the Euclidean projection of Table 2 row 4
+    assert np.allclose(px.proj_l2ball_metric(z, y, eps, np.ones(m), 20), px.proj_l2ball(z, y, eps), atol=1e-14)
+    # inverse-density-like weights spanning two decades
+    U = 1.0 / rng.integers(1, 100, m)
+    ref = _metric_projection_closed_form(z, y, eps, U)
+    x = px.proj_l2ball_metric(z, y, eps, U, 5000)
+    assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref - y)
+    x20 = px.proj_l2ball_metric(z, y, eps, U, 20)
+    assert np.linalg.norm(x20 - y) <= eps * (1 + 1e-12)                   # feasible
+    # the metric distance decreases along the sub-iterations
+    d = lambda a: np.real(np.vdot(a - z, U * (a - z)))
+    assert d(ref) <= d(x20) + 1e-9 <= d(px.proj_l2ball(z, y, eps)) + 1e-9
+    # inside the ball nothing moves; the preconditioned dual is then zero
+    zin = y + 0.1 * (z - y) / np.linalg.norm(z - y)
+    assert np.allclose(px.proj_l2ball_metric(zin, y, eps, U, 20), zin)
+    v = px.dual_l2ball_precond(U * (zin - y), y, y, eps, U, 20)        # z = v / U + y = zin
+    assert np.allclose(v, 0.0, atol=1e-12)
+
+
+def test_inverse_density_by_counting():
+    from oracle import pdfb as pd
+    rng = np.random.default_rng(3)
+    n = 8
+    uv = rng.uniform(-np.pi, np.pi, (200, 2))
+    U = pd.inverse_density(uv, n, n)
+    K = 2 * n
+    cells = [(int(np.floor(v * K / (2 * np.pi) + 0.5)) % K, int(np.floor(u * K / (2 * np.pi) + 0.5)) % K)
+             for u, v in uv]
+    for i, c in enumerate(cells):
+        assert U[i] == 1.0 / sum(1 for d in cells if d == c)
