@@ -208,6 +208,20 @@ fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta
 fhs_status fhs_heuristic_params(fhs_ctx* ctx, int32_t cube, const double* sigma, int32_t power_iters, double rel_tol,
                                 double* eta_out, double* eps_out, double* mu_out, double* mu_bar_out);
 
+/* Preconditioned data duals of a cube (Section 3.2; Algorithm 2 v line with
+ * U_{l,b} != I): v <- U (I - prox^U_B)(U^-1 v + Phi x_check), the U-metric projection
+ * onto B(y_{l,b}, eps_{l,b}) approximated by n_sub forward-backward sub-iterations
+ * w <- P_B(w - gamma U (w - z)), gamma = 1 / max U over the block, started from the
+ * Euclidean projection P_B(z).  U: host [n_vis] in the caller's order, finite, > 0, or
+ * NULL for the inverse sampling density: U = 1 / (number of the channel's visibilities
+ * whose nearest cell of the 2n1 x 2n2 grid, round(omega K / 2 pi) mod K, is the
+ * visibility's own).  n_sub = 0 returns to U = I (closed-form projections).  While
+ * n_sub > 0, fhs_opnorm_sq and fhs_heuristic_params return ||U^1/2 Phi_l||^2 and
+ * eta_l = 1 / ||U^1/2 Phi_l||^2 (Section 3.2); set eta with one of them afterwards.
+ * fhs_proj_l2ball_blocks stays the Euclidean projection.  Synchronising.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+fhs_status fhs_set_preconditioning(fhs_ctx* ctx, int32_t cube, int32_t n_sub, const float* U);
+
 /* Replace the algorithm parameters of a cube (same meaning and host arrays as in
  * fhs_cube_desc: eta [L], mu_bar [Qy*Qx], eps [L*B]).  Lets a caller compute
  * eta = 1/||Phi_l||^2 with fhs_opnorm_sq and the noise-based heuristics

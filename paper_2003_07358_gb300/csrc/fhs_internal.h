@@ -74,6 +74,11 @@ struct Cube {
   float* d_scale_c = nullptr;                // [n2]
   double* d_eps = nullptr;                   // [L*B]
   int64_t* d_M_lb = nullptr;                 // [L*B] visibilities per (channel, block)
+  // preconditioned data duals (Section 3.2): n_sub forward-backward sub-iterations
+  // (0: U = I, Euclidean projections), U per visibility (internal order), gamma per block
+  int n_sub = 0;
+  float* d_U = nullptr;                      // [n_vis]
+  float* d_gamma = nullptr;                  // [L*B] 1 / max U of the block
   float* d_eta = nullptr;                    // [L]
   float* d_mubar = nullptr;                  // [Q]
   // TMA descriptors of the degridder's tile staging over the context's grid scratch,
@@ -94,6 +99,7 @@ struct Scratch {
   float* img = nullptr;      size_t img_elems = 0;      // [L][n1][n2]
   float* img2 = nullptr;
   float2* vis = nullptr;     size_t vis_elems = 0;      // [n_vis]
+  float2* vis2 = nullptr;                               // [n_vis] forward-backward iterate (preconditioning)
   double* red = nullptr;     size_t red_elems = 0;      // reduction partials
   double* red_host = nullptr;                           // pinned host copy
   double* gram = nullptr;    size_t gram_elems = 0;     // nuclear Gram partials (FP64)
@@ -132,6 +138,7 @@ struct fhs_ctx {
   int timer = FHS_TIMER_NONE;
   bool timer_off = false;          // true while fhs_solve captures (no event nodes in its loops)
   void* solve_dev = nullptr;       // [ncubes] device control states of fhs_solve
+  uint64_t param_version = 0;      // bumped by calls that change what an iteration graph holds
   std::vector<cudaEvent_t> tev;
   bool timer_armed = false;
 };
@@ -173,6 +180,8 @@ void launch_grid_count(const Cube& cb, cudaStream_t st);
 void launch_l2ball_partials(const Cube& cb, const float2* z, const float2* y, float2* d,
                             double* partials, int nparts, cudaStream_t st);
 void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, float2* v, cudaStream_t st);
+void launch_precond_duals(const Cube& cb, float2* d, float2* t, float* blk_scale, double* partials, cudaStream_t st);
+void launch_vis_scale(float2* v, const float* f, int64_t n, bool divide, cudaStream_t st);
 void launch_vis_gather(const int64_t* perm, int64_t n, const float2* in, float2* out, cudaStream_t st);
 void launch_vis_scatter(const int64_t* perm, int64_t n, const float2* in, float2* out, cudaStream_t st);
 

@@ -500,7 +500,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
 
 void free_cube(Cube& cb) {
   void* ps[] = {cb.d_uv, cb.d_blk, cb.d_perm, cb.d_vis_off, cb.d_tile_off, cb.d_facets, cb.d_win, cb.d_win64, cb.d_tile_of,
-                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar, cb.d_ncmax, cb.d_M_lb};
+                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar, cb.d_ncmax, cb.d_M_lb, cb.d_U, cb.d_gamma};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -556,7 +556,8 @@ void alloc_scratch(fhs_ctx* ctx) {
 }
 
 void free_scratch(Scratch& s) {
-  void* ps[] = {s.grid, s.pack, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.img2, s.vis, s.red, s.gram, s.nucM, s.blk_scale,
+  void* ps[] = {s.grid, s.pack, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.img2, s.vis, s.vis2, s.red, s.gram, s.nucM,
+                s.blk_scale,
                 s.blk_out, s.ll1, s.stat};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -636,6 +637,8 @@ void pdfb_iteration_cube(fhs_ctx* ctx, int c, const fhs_iterate& a) {
     check_launch("nuclear Gram");
     FHS_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
     launch_fft_forward(ctx, cb, a.X, ctx->s.grid, st);
+    // preconditioned duals (Section 3.2): the degridder forms d = U^-1 v + Phi x_check - y
+    if (cb.n_sub > 0) launch_vis_scale((float2*)a.state.v, cb.d_U, cb.n_vis, true, st);
     int np;
     if (use_fast(ctx, cb)) {
       np = degrid_tiled_parts(cb);
@@ -649,8 +652,15 @@ void pdfb_iteration_cube(fhs_ctx* ctx, int c, const fhs_iterate& a) {
                          (float2*)a.state.u_prev, ctx->s.red, np, st);
     }
     launch_block_finalize(cb, ctx->s.red, np, ctx->s.blk_scale, stat + 2 * pp, st);
+    const float* gscale = ctx->s.blk_scale;
+    if (cb.n_sub > 0) {
+      // U-metric projections by forward-backward sub-iterations; s.vis <- v = U (d - w)
+      launch_precond_duals(cb, ctx->s.vis, ctx->s.vis2, ctx->s.blk_scale, ctx->s.red, st);
+      check_launch("preconditioned duals");
+      gscale = nullptr;
+    }
     timer_mark(ctx, FHS_TIMER_GRID, 2 * c);
-    launch_grid(cb, ctx->s.vis, ctx->s.blk_scale, (float2*)a.state.v, ctx->s.grid, st);
+    launch_grid(cb, ctx->s.vis, gscale, (float2*)a.state.v, ctx->s.grid, st);
     timer_mark(ctx, FHS_TIMER_GRID, 2 * c + 1);
     launch_fft_adjoint(ctx, cb, ctx->s.grid, A, cb.d_eta, false, st);
     check_launch("adjoint");
@@ -794,6 +804,7 @@ void opnorm_sq(fhs_ctx* ctx, const Cube& cb, int32_t max_iter, double rel_tol, d
   double* dinv = ctx->s.blk_out;   // L doubles of scratch
   for (int it = 0; it < max_iter; ++it) {
     launch_measure(ctx, cb, ctx->s.img2, ctx->s.vis, st);
+    if (cb.n_sub > 0) launch_vis_scale(ctx->s.vis, cb.d_U, cb.n_vis, false, st);   // ||U^1/2 Phi||^2
     adjoint_into(ctx, cb, ctx->s.vis, nullptr, nullptr, ctx->s.img, nullptr, false);
     launch_sumsq(ctx->s.img, N, L, ctx->s.red, np, st);
     check_launch("power method");
@@ -1138,6 +1149,69 @@ fhs_status fhs_solve(fhs_ctx* ctx, const fhs_iterate* it, const fhs_solve_params
   });
 }
 
+fhs_status fhs_set_preconditioning(fhs_ctx* ctx, int32_t cube, int32_t n_sub, const float* U_user) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(cube >= 0 && cube < (int32_t)ctx->cubes.size(), FHS_ERR_INVALID_ARG, "cube index out of range");
+    FHS_REQUIRE(n_sub >= 0 && n_sub <= 1000, FHS_ERR_INVALID_ARG, "n_sub must be in [0, 1000]");
+    Cube& cb = ctx->cubes[cube];
+    cudaStream_t st = ctx->stream;
+    FHS_CUDA(cudaStreamSynchronize(st));
+    ctx->param_version++;
+    if (n_sub == 0) {
+      cb.n_sub = 0;
+      return;
+    }
+    const int64_t n = cb.n_vis;
+    std::vector<float> U(n);
+    std::vector<uint8_t> blk(n);
+    if (n) FHS_CUDA(cudaMemcpy(blk.data(), cb.d_blk, n, cudaMemcpyDeviceToHost));
+    if (U_user) {
+      for (int64_t i = 0; i < n; ++i) {
+        const float u = U_user[cb.perm_host[i]];
+        FHS_REQUIRE(std::isfinite(u) && u > 0.f, FHS_ERR_INVALID_ARG, "U must be finite and > 0");
+        U[i] = u;
+      }
+    } else {
+      // inverse sampling density: 1 / (visibilities of the channel whose nearest cell of
+      // the oversampled grid, round(omega K / 2 pi) mod K, is the visibility's own)
+      std::vector<float2> uv(n);
+      if (n) FHS_CUDA(cudaMemcpy(uv.data(), cb.d_uv, n * sizeof(float2), cudaMemcpyDeviceToHost));
+      std::vector<int64_t> cell;
+      std::vector<int64_t> sorted;
+      for (int l = 0; l < cb.L; ++l) {
+        const int64_t o = cb.vis_off[l], m = cb.vis_off[l + 1] - o;
+        cell.resize(m);
+        for (int64_t j = 0; j < m; ++j) {
+          const double tr = floor((double)uv[o + j].y * cb.K1 / (2.0 * kPi) + 0.5);
+          const double tc = floor((double)uv[o + j].x * cb.K2 / (2.0 * kPi) + 0.5);
+          const int64_t r = (((int64_t)tr % cb.K1) + cb.K1) % cb.K1, c = (((int64_t)tc % cb.K2) + cb.K2) % cb.K2;
+          cell[j] = r * cb.K2 + c;
+        }
+        sorted = cell;
+        std::sort(sorted.begin(), sorted.end());
+        for (int64_t j = 0; j < m; ++j) {
+          auto rng = std::equal_range(sorted.begin(), sorted.end(), cell[j]);
+          U[o + j] = (float)(1.0 / (double)(rng.second - rng.first));
+        }
+      }
+    }
+    std::vector<float> gmax(cb.L * cb.B, 0.f), gamma(cb.L * cb.B, 0.f);
+    for (int l = 0; l < cb.L; ++l)
+      for (int64_t i = cb.vis_off[l]; i < cb.vis_off[l + 1]; ++i) {
+        float& g = gmax[l * cb.B + blk[i]];
+        g = std::max(g, U[i]);
+      }
+    for (int k = 0; k < cb.L * cb.B; ++k) gamma[k] = gmax[k] > 0.f ? 1.f / gmax[k] : 0.f;
+    if (!cb.d_U) cb.d_U = dalloc<float>(n);
+    if (!cb.d_gamma) cb.d_gamma = dalloc<float>(gamma.size());
+    if (!ctx->s.vis2) ctx->s.vis2 = dalloc<float2>(ctx->s.vis_elems);
+    upload(cb.d_U, U.data(), U.size(), st);
+    upload(cb.d_gamma, gamma.data(), gamma.size(), st);
+    FHS_CUDA(cudaStreamSynchronize(st));
+    cb.n_sub = n_sub;
+  });
+}
+
 fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, double kappa, const double* eta,
                           double mu, const double* mu_bar, const double* eps) {
   return guarded(ctx, [&] {
@@ -1213,6 +1287,7 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
     std::vector<const void*> key;
     key.push_back((const void*)(intptr_t)ctx->path);
     key.push_back((const void*)(intptr_t)ctx->timer);
+    key.push_back((const void*)(uintptr_t)ctx->param_version);
     for (int c = 0; c < nc; ++c) {
       const fhs_iterate& a = it[c];
       FHS_REQUIRE(a.X && a.Xcheck && a.y && a.state.W && a.state.theta && a.state.P && a.state.theta_bar &&

@@ -758,6 +758,63 @@ __global__ void __launch_bounds__(256) k_l2ball_partials(const float2* __restric
   block_partials<8>(v0, 0.0, b, valid, B, sred, partials + ((size_t)l * nparts + blockIdx.x) * 2 * B);
 }
 
+// ------------------------------------------------- preconditioned data duals
+// Algorithm 2 v line with a diagonal metric U (Section 3.2), in terms of
+// d = U^-1 v + Phi x_check - y (from the degridder, after v <- v / U) and w = x - y:
+//   w_0 = P(d),  w_k = P(w_{k-1} - gamma U (w_{k-1} - d))  (k = 1..n_sub),  v = U (d - w),
+// with P the projection onto the ball of radius eps_{l,b} centred at 0 and
+// gamma = 1 / max U over the block: forward-backward sub-iterations of the U-metric
+// projection.  A step stores t_k = w_{k-1} - gamma U (w_{k-1} - d) and the block partial
+// sums of |t_k|^2; k_block_finalize turns them into s_k (P(t_k) = t_k (1 - s_k)), which
+// the next step or the final kernel applies.
+__global__ void __launch_bounds__(256) k_fb_step(const float2* __restrict__ d, float2* __restrict__ t,
+                                                 const float* __restrict__ U, const float* __restrict__ gamma,
+                                                 const float* __restrict__ scale_prev, const uint8_t* __restrict__ blk,
+                                                 const int64_t* __restrict__ vis_off, int B, int first,
+                                                 double* __restrict__ partials, int nparts) {
+  __shared__ double sred[8 * 2 * kMaxB];
+  const int l = blockIdx.y;
+  const int64_t i = vis_off[l] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < vis_off[l + 1];
+  double v0 = 0.0;
+  int b = 0;
+  if (valid) {
+    b = blk[i];
+    const int kb = l * B + b;
+    const float2 dd = d[i];
+    const float keep = 1.f - scale_prev[kb];          // min(1, eps / ||.||) of the previous iterate
+    const float2 src = first ? dd : t[i];
+    const float2 w = make_float2(src.x * keep, src.y * keep);
+    const float g = gamma[kb] * U[i];
+    const float2 tn = make_float2(w.x - g * (w.x - dd.x), w.y - g * (w.y - dd.y));
+    t[i] = tn;
+    v0 = (double)tn.x * tn.x + (double)tn.y * tn.y;
+  }
+  block_partials<8>(v0, 0.0, b, valid, B, sred, partials + ((size_t)l * nparts + blockIdx.x) * 2 * B);
+}
+
+// v = U (d - P(t_n)), written over d.
+__global__ void k_fb_final(float2* __restrict__ d, const float2* __restrict__ t, const float* __restrict__ U,
+                           const float* __restrict__ scale, const uint8_t* __restrict__ blk,
+                           const int64_t* __restrict__ vis_off, int B) {
+  const int l = blockIdx.y;
+  const int64_t i = vis_off[l] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= vis_off[l + 1]) return;
+  const float keep = 1.f - scale[l * B + blk[i]];
+  const float2 tt = t[i], dd = d[i];
+  const float u = U[i];
+  d[i] = make_float2(u * (dd.x - tt.x * keep), u * (dd.y - tt.y * keep));
+}
+
+// v <- v * f or v <- v / f elementwise (f > 0).
+__global__ void k_vis_scale(float2* __restrict__ v, const float* __restrict__ f, int64_t n, int divide) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float s = divide ? 1.f / f[i] : f[i];
+  const float2 a = v[i];
+  v[i] = make_float2(a.x * s, a.y * s);
+}
+
 // Per (channel, block): sum the CTA partials in order; scale = max(0, 1 - eps/||d||);
 // out[2][L*B] = (||d||, ||y - u||) in FP64.
 // One CTA per (channel, block): the CTA partials are summed in a fixed order
@@ -1103,6 +1160,24 @@ void launch_block_finalize(const Cube& cb, const double* partials, int nparts, f
                            cudaStream_t st) {
   int n = cb.L * cb.B;
   k_block_finalize<<<n, 256, 0, st>>>(partials, nparts, cb.B, cb.L, cb.d_eps, scale, out);
+  note_launches(1);
+}
+
+void launch_precond_duals(const Cube& cb, float2* d, float2* t, float* blk_scale, double* partials, cudaStream_t st) {
+  const int np = degrid_parts(cb);
+  dim3 grd(np, cb.L);
+  for (int k = 0; k < cb.n_sub; ++k) {
+    k_fb_step<<<grd, 256, 0, st>>>(d, t, cb.d_U, cb.d_gamma, blk_scale, cb.d_blk, cb.d_vis_off, cb.B, k == 0 ? 1 : 0,
+                                   partials, np);
+    launch_block_finalize(cb, partials, np, blk_scale, nullptr, st);
+    note_launches(1);
+  }
+  k_fb_final<<<grd, 256, 0, st>>>(d, t, cb.d_U, blk_scale, cb.d_blk, cb.d_vis_off, cb.B);
+  note_launches(1);
+}
+
+void launch_vis_scale(float2* v, const float* f, int64_t n, bool divide, cudaStream_t st) {
+  if (n > 0) k_vis_scale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, f, n, divide ? 1 : 0);
   note_launches(1);
 }
 

@@ -26,7 +26,7 @@ SYMBOLS = [
     "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_prox_l21_sara_facets", "fhs_prox_nuclear_facets",
     "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
     "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path", "fhs_set_kernel_timer",
-    "fhs_kernel_timer_read", "fhs_solve", "fhs_heuristic_params",
+    "fhs_kernel_timer_read", "fhs_solve", "fhs_heuristic_params", "fhs_set_preconditioning",
 ]
 MAX_SOLVE_CYCLES = 32
 FHS_PATH = {"fast": 0, "plain": 1}
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
         "fhs_kernel_timer_read": ([vp, C.POINTER(C.c_double), C.POINTER(i32)], i32),
         "fhs_solve": ([vp, C.POINTER(fhs_iterate), C.POINTER(fhs_solve_params), C.POINTER(fhs_solve_report)], i32),
         "fhs_heuristic_params": ([vp, i32, dp, i32, C.c_double, dp, dp, dp, dp], i32),
+        "fhs_set_preconditioning": ([vp, i32, i32, C.POINTER(C.c_float)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -352,6 +353,18 @@ class Context:
                                                   eta.ctypes.data_as(P), eps.ctypes.data_as(P),
                                                   mu.ctypes.data_as(P), mub.ctypes.data_as(P)))
         return {"eta": eta, "eps": eps.reshape(L, B), "mu": float(mu[0]), "mu_bar": mub}
+
+    def fhs_set_preconditioning(self, cube, n_sub: int, U=None):
+        """Preconditioned data duals (n_sub forward-backward sub-iterations; U in the
+        caller's visibility order, or None for the inverse sampling density); n_sub = 0
+        returns to Euclidean projections."""
+        if U is None:
+            self._check(self.lib.fhs_set_preconditioning(self.h, cube, n_sub, None))
+            return
+        u = np.ascontiguousarray(U, dtype=np.float32).ravel()
+        if u.size != self.sizes(cube)["n_vis"]:
+            raise ValueError("U must have one entry per visibility of the cube")
+        self._check(self.lib.fhs_set_preconditioning(self.h, cube, n_sub, u.ctypes.data_as(C.POINTER(C.c_float))))
 
     def fhs_set_params(self, cube, tau, zeta, kappa, eta, mu, mu_bar, eps):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (eta, mu_bar, eps)]
