@@ -229,9 +229,10 @@ fhs_status fhs_set_preconditioning(fhs_ctx* ctx, int32_t cube, int32_t n_sub, co
 fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, double kappa, const double* eta,
                           double mu, const double* mu_bar, const double* eps);
 /* Kernel path used by fhs_pdfb_iter, fhs_prox_l21_sara_facets and fhs_reweight:
- * FHS_PATH_FAST (default) uses the fused kernels; FHS_PATH_PLAIN the
- * unfused one-launch-per-pass kernels (the FP32 reference path that the fused
- * one is measured against).  Both compute the same operators. */
+ * FHS_PATH_FAST (default) uses the fused kernels, the tensor-core facet Grams and one
+ * CUDA graph per iteration; FHS_PATH_PLAIN the unfused one-launch-per-pass kernels,
+ * the CUDA-core float-float Grams and direct launches without a graph (the FP32
+ * path that the fast one is measured against).  Both compute the same operators. */
 enum { FHS_PATH_FAST = 0, FHS_PATH_PLAIN = 1 };
 fhs_status fhs_set_path(fhs_ctx* ctx, int32_t path);
 /* Number of CUDA kernels this library has launched in this process so far. */
@@ -255,6 +256,15 @@ fhs_status fhs_kernel_timer_read(fhs_ctx* ctx, double* ms_total, int32_t* launch
  * stats: host [ncubes] or NULL; when not NULL the call synchronises and
  * fills the statistics of the last iteration. */
 fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fhs_iter_stats* stats);
+
+/* The same iterations with the data and the result in HOST memory: for every cube,
+ * y_host[c] (complex64, [n_vis], the caller's visibility order) is copied to the
+ * device and put in internal order (into it[c].y, which must be a device array of
+ * n_vis complex64), n_iter iterations run as in fhs_pdfb_iter, and it[c].X is copied
+ * back to X_host[c] ([L][n1][n2] float).  Host buffers may be pageable or pinned
+ * (pinned ones copy faster).  Synchronising.  Errors: as fhs_pdfb_iter. */
+fhs_status fhs_pdfb_iter_host(fhs_ctx* ctx, const fhs_iterate* it, const float* const* y_host, float* const* X_host,
+                              int32_t n_iter, fhs_iter_stats* stats);
 
 /* ------------------------------------------- Algorithm 1 with stopping rules */
 /* Stopping rules of Algorithm 2 (PDFB runs while p < p_min, or p < p_max and

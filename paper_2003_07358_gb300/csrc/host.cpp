@@ -1093,6 +1093,34 @@ fhs_status fhs_reweight(fhs_ctx* ctx, int32_t cube, const float* x, float* theta
   });
 }
 
+fhs_status fhs_pdfb_iter_host(fhs_ctx* ctx, const fhs_iterate* it, const float* const* y_host, float* const* X_host,
+                              int32_t n_iter, fhs_iter_stats* stats) {
+  fhs_status rc = guarded(ctx, [&] {
+    FHS_REQUIRE(it && y_host && X_host && n_iter >= 0, FHS_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t st = ctx->stream;
+    for (int c = 0; c < (int)ctx->cubes.size(); ++c) {
+      const Cube& cb = ctx->cubes[c];
+      FHS_REQUIRE(y_host[c] && X_host[c] && it[c].y, FHS_ERR_INVALID_ARG, "NULL array");
+      // caller's order -> internal order through the visibility scratch
+      FHS_CUDA(cudaMemcpyAsync(ctx->s.vis, y_host[c], (size_t)cb.n_vis * sizeof(float2), cudaMemcpyHostToDevice, st));
+      launch_vis_gather(cb.d_perm, cb.n_vis, ctx->s.vis, (float2*)it[c].y, st);
+      check_launch("vis_to_internal");
+    }
+  });
+  if (rc != FHS_OK) return rc;
+  rc = fhs_pdfb_iter(ctx, it, n_iter, stats);
+  if (rc != FHS_OK) return rc;
+  return guarded(ctx, [&] {
+    cudaStream_t st = ctx->stream;
+    for (int c = 0; c < (int)ctx->cubes.size(); ++c) {
+      const Cube& cb = ctx->cubes[c];
+      FHS_CUDA(cudaMemcpyAsync(X_host[c], it[c].X, (size_t)cb.L * cb.n1 * cb.n2 * sizeof(float),
+                               cudaMemcpyDeviceToHost, st));
+    }
+    FHS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
 fhs_status fhs_solve(fhs_ctx* ctx, const fhs_iterate* it, const fhs_solve_params* prm, fhs_solve_report* report) {
   return guarded(ctx, [&] {
     FHS_REQUIRE(it && prm && report, FHS_ERR_INVALID_ARG, "NULL argument");
@@ -1298,6 +1326,10 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
       key.insert(key.end(), ps, ps + 9);
     }
     if (n_iter == 0) return;
+    if (ctx->path == FHS_PATH_PLAIN) {
+      // the comparison arm: direct launches, no graph
+      for (int p = 0; p < n_iter; ++p) pdfb_iteration(ctx, it);
+    } else {
     // (re)capture one iteration of every cube into a CUDA graph when the arrays or the path change
     if (!ctx->graph_exec || key != ctx->graph_key) {
       if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
@@ -1333,6 +1365,7 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
     }
     FHS_CUDA(cudaEventRecord(ctx->ev_out, ctx->gstream));
     FHS_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0));
+    }
     if (ctx->timer != FHS_TIMER_NONE) ctx->timer_armed = true;
     if (!stats) return;
     std::vector<double> h(ctx->s.stat_stride * nc);

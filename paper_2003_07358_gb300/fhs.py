@@ -27,6 +27,7 @@ SYMBOLS = [
     "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
     "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path", "fhs_set_kernel_timer",
     "fhs_kernel_timer_read", "fhs_solve", "fhs_heuristic_params", "fhs_set_preconditioning",
+    "fhs_pdfb_iter_host",
 ]
 MAX_SOLVE_CYCLES = 32
 FHS_PATH = {"fast": 0, "plain": 1}
@@ -118,6 +119,8 @@ def load(path: str = LIB_PATH):
         "fhs_solve": ([vp, C.POINTER(fhs_iterate), C.POINTER(fhs_solve_params), C.POINTER(fhs_solve_report)], i32),
         "fhs_heuristic_params": ([vp, i32, dp, i32, C.c_double, dp, dp, dp, dp], i32),
         "fhs_set_preconditioning": ([vp, i32, i32, C.POINTER(C.c_float)], i32),
+        "fhs_pdfb_iter_host": ([vp, C.POINTER(fhs_iterate), C.POINTER(vp), C.POINTER(vp), i32,
+                                C.POINTER(fhs_iter_stats)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -133,6 +136,19 @@ def _ptr(t) -> int | None:
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("libfhs takes contiguous CUDA tensors")
     return t.data_ptr()
+
+
+def _host_ptr(a, dtype) -> int:
+    """Address of a contiguous host array (torch CPU tensor or numpy array) of `dtype`."""
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+        if str(a.dtype).replace("torch.", "") != np.dtype(dtype).name:
+            raise ValueError(f"host buffer must be {np.dtype(dtype).name}")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise ValueError(f"host buffers must be contiguous {np.dtype(dtype).name} arrays")
+    return a.ctypes.data
 
 
 def _check_noalloc_args(z, y, seg_off: np.ndarray, eps: np.ndarray, v_out) -> None:
@@ -365,6 +381,20 @@ class Context:
         if u.size != self.sizes(cube)["n_vis"]:
             raise ValueError("U must have one entry per visibility of the cube")
         self._check(self.lib.fhs_set_preconditioning(self.h, cube, n_sub, u.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def fhs_pdfb_iter_host(self, iterates: list[dict], y_host: list, X_host: list, n_iter: int,
+                           want_stats: bool = True):
+        """fhs_pdfb_iter with the data (complex64, caller's order) and the result (float32
+        images) in host memory: CPU tensors or numpy arrays, contiguous."""
+        arr = self._iterates(iterates)
+        n = len(iterates)
+        yp = (C.c_void_p * n)(*[_host_ptr(a, np.complex64) for a in y_host])
+        xp = (C.c_void_p * n)(*[_host_ptr(a, np.float32) for a in X_host])
+        stats = (fhs_iter_stats * n)() if want_stats else None
+        self._check(self.lib.fhs_pdfb_iter_host(self.h, arr, yp, xp, n_iter, stats))
+        if not want_stats:
+            return None
+        return [{"xi": s.xi, "res_norm": s.res_norm, "eps_norm": s.eps_norm} for s in stats]
 
     def fhs_set_params(self, cube, tau, zeta, kappa, eta, mu, mu_bar, eps):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (eta, mu_bar, eps)]

@@ -103,3 +103,20 @@ def test_solve_reports_nonfinite_data(tiny):
     rep = ctx.fhs_solve(it2, p_min=2, p_max=2, xi_pdfb=0.0, res_factor=1.0, t_max=1, xi_reweight=0.0)[0]
     assert rep["iterations"] == 2 and not rep["nonfinite"]
     ctx.close()
+
+
+def test_host_buffer_iterations_match_device_ones(tiny):
+    """fhs_pdfb_iter_host (data and result in host memory, caller's order) gives the
+    iterates of fhs_pdfb_iter on the same data, bit for bit."""
+    spec, inp, prob = tiny
+    ctx = make_context(prob, torch)
+    it1 = _iterate(ctx, prob, prob.y)
+    s1 = ctx.fhs_pdfb_iter(it1, 5)
+    X = torch.zeros((prob.L, prob.n1, prob.n2), device="cuda")
+    it2 = [{"X": X, "Xcheck": torch.zeros_like(X), "y": torch.empty_like(it1[0]["y"]), "state": ctx.new_state(0)}]
+    y_host = torch.as_tensor(np.ascontiguousarray(prob.y, dtype=np.complex64)).pin_memory()
+    X_host = torch.empty((prob.L, prob.n1, prob.n2), dtype=torch.float32).pin_memory()
+    s2 = ctx.fhs_pdfb_iter_host(it2, [y_host], [X_host], 5)
+    assert torch.equal(X_host, it1[0]["X"].cpu())
+    assert s1[0]["xi"] == s2[0]["xi"]
+    ctx.close()
