@@ -303,6 +303,32 @@ typedef struct {
  * CUDA.  The kernel timer (fhs_set_kernel_timer) records nothing inside fhs_solve. */
 fhs_status fhs_solve(fhs_ctx* ctx, const fhs_iterate* it, const fhs_solve_params* prm, fhs_solve_report* report);
 
+/* ----------------------------------------------------------- checkpoints */
+/* Save / restore the state of Algorithms 1-2 (the warm start of Algorithm 1: X,
+ * X_check, W, theta, P, theta_bar, v, u_prev of every cube, and each cube's parameters
+ * tau, zeta, kappa, mu, eta, mu_bar, eps) to a file.  Loading checks the file's
+ * version, a 64-bit hash of its contents and that every cube has the context's shape
+ * before anything is changed; the iterations then continue exactly where they
+ * stopped (the data y and the preconditioner are the caller's to set again).  The
+ * arrays are copied through host memory in 64 MB pieces.  Synchronising.
+ * Errors: INVALID_ARG (path, I/O, wrong or corrupt file, other shape), CUDA. */
+fhs_status fhs_checkpoint_save(fhs_ctx* ctx, const fhs_iterate* it, const char* path);
+fhs_status fhs_checkpoint_load(fhs_ctx* ctx, const fhs_iterate* it, const char* path);
+
+/* ------------------------------------------------ fault-injection hooks */
+/* For tests of the error paths without faulting a GPU.  fhs_set_wait_limit shortens
+ * the first phase of every bounded device-side wait (TMA copies, tensor-core MMAs) to
+ * `spins` polls (0 restores the default, about 4 M; -1 gives up without polling, so every
+ * such wait reports a timeout); the second phase, which lets copies
+ * and MMAs in flight land before a kernel moves on, keeps its full length.  A wait that
+ * runs out sets the device status word: the next synchronising call returns
+ * FHS_ERR_TIMEOUT and the outputs of that call are undefined; later calls work.
+ * fhs_set_alloc_limit caps the device bytes the library allocates on the calling thread
+ * from the start of each fhs_create (0: no cap); a request beyond it fails with
+ * FHS_ERR_OOM.  Both apply process-wide. */
+fhs_status fhs_set_wait_limit(int64_t spins);
+fhs_status fhs_set_alloc_limit(uint64_t bytes);
+
 /* ------------------------------------------------- allocation-free variant */
 /* The paper has no counterpart of this entry point: it serves callers that may
  * not allocate device memory (a host application that owns all device memory

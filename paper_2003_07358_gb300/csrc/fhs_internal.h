@@ -210,6 +210,10 @@ void launch_nuclear_apply(fhs_ctx* ctx, const Cube& cb, const float* xcheck, flo
 bool launch_gram_tc(const Cube& cb, const float* xcheck, const float* P, double* part, int nchunk_max,
                     cudaStream_t st);
 unsigned read_gram_status(bool clear);
+cudaError_t set_gram_wait_first(long long spins);
+// first phase of every bounded device-side wait (0: default); the drain waits keep
+// their full length
+cudaError_t set_wait_first(long long spins);
 
 // device control of Algorithms 1-2 (solve.cu); the state is an opaque device struct
 size_t solve_state_bytes();

@@ -37,6 +37,7 @@
 namespace fhs {
 
 __device__ unsigned int g_gram_status = 0;
+__device__ long long g_gram_wait_first = 0;   // first wait's length (0: kGramSpinLimit)
 constexpr unsigned kGramTimeout = 1u;
 constexpr long long kGramSpinLimit = 1ll << 24;
 
@@ -60,8 +61,11 @@ __device__ __forceinline__ uint64_t tc_smem_desc(unsigned saddr) {
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcRows >> 3) << 17) |
                               ((uint32_t)(kTcRows >> 4) << 24);
 
-__device__ __forceinline__ bool tc_mbar_wait(unsigned bar, unsigned parity) {
-  for (long long it = 0; it < kGramSpinLimit; ++it) {
+__device__ __forceinline__ bool tc_mbar_wait(unsigned bar, unsigned parity, bool first = true) {
+  const long long lim = !first ? kGramSpinLimit
+                        : g_gram_wait_first > 0 ? g_gram_wait_first
+                        : g_gram_wait_first < 0 ? 0 : kGramSpinLimit;
+  for (long long it = 0; it < lim; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -114,6 +118,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
   unsigned char* opnd = tc_smem;                                                 // 2 stages
   double* red = reinterpret_cast<double*>(tc_smem);                              // [NH][4][LP][LP]
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar_drain;  // completes when every MMA issued so far has
   __shared__ uint32_t tmem_base;
   __shared__ int s_max[NH][LP];                // per (half-chunk, channel) max |z| (float bits)
   __shared__ float s_scale[NH][LP];
@@ -136,6 +141,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar_drain)));
     asm volatile("fence.mbarrier_init.release.cluster;\n");
   }
   for (int i = tid; i < NH * LP; i += kTcThreads) (&s_max[0][0])[i] = 0;
@@ -269,9 +275,15 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
   if (__syncthreads_or(!ok)) {
     // a wait gave up: flag it, give the MMAs a second bounded chance to land, then free
     // the tensor memory and leave (the partial of this chunk is not written)
-    if (tid == 0) atomicOr(&g_gram_status, kGramTimeout);
-    tc_mbar_wait(smem_u32(&mbar[0]), phase[0]);
-    tc_mbar_wait(smem_u32(&mbar[1]), phase[1]);
+    // (the threads may disagree on the pending phases of mbar[]: a fresh commit to the
+    // drain barrier tracks every MMA issued so far, and its first phase is the one)
+    if (tid == 0) {
+      atomicOr(&g_gram_status, kGramTimeout);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&mbar_drain))
+                   : "memory");
+    }
+    tc_mbar_wait(smem_u32(&mbar_drain), 0u, false);
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128u));
@@ -367,6 +379,10 @@ bool launch_gram_tc(const Cube& cb, const float* xcheck, const float* P, double*
   }
   note_launches(1);
   return true;
+}
+
+cudaError_t set_gram_wait_first(long long spins) {
+  return cudaMemcpyToSymbol(g_gram_wait_first, &spins, sizeof(spins));
 }
 
 unsigned read_gram_status(bool clear) {

@@ -267,11 +267,20 @@ void nuclear_axis(int n, int Q, double rho, int kind, std::vector<int>& start, s
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Fault-injection hook: a cap on the device bytes the library allocates on this thread
+// from the start of the last fhs_create (0: none); a request beyond it fails as OOM.
+std::atomic<uint64_t> g_alloc_limit{0};
+thread_local uint64_t g_alloc_used = 0;
+
 template <class T>
 T* dalloc(size_t n) {
   T* p = nullptr;
   if (n == 0) n = 1;
+  const uint64_t lim = g_alloc_limit.load();
+  if (lim && g_alloc_used + n * sizeof(T) > lim)
+    throw Fail{FHS_ERR_OOM, "device allocation limit of " + std::to_string(lim) + " bytes reached"};
   FHS_CUDA(cudaMalloc((void**)&p, n * sizeof(T)));
+  g_alloc_used += n * sizeof(T);
   return p;
 }
 
@@ -834,6 +843,65 @@ void opnorm_sq(fhs_ctx* ctx, const Cube& cb, int32_t max_iter, double rel_tol, d
 
 }  // namespace
 
+namespace {
+// ------------------------------------------------------------ checkpoints
+// File: "FHSCKPT1", ncubes (int64), per cube its shape (n1, n2, L, B, Qy, Qx, n_vis, I,
+// facet pixels, n_sub: int64) and parameters (tau, zeta, kappa, mu, eta[L], mu_bar[Q],
+// eps[L B]: double), then the arrays X, Xcheck, W, theta, P, theta_bar, v, u_prev of every
+// cube, then the FNV-1a 64 hash of everything after the magic.
+constexpr char kCkptMagic[8] = {'F', 'H', 'S', 'C', 'K', 'P', 'T', '1'};
+constexpr size_t kCkptChunk = (size_t)64 << 20;
+
+struct Fnv {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+  }
+};
+
+struct CkptArray {
+  void* dev;
+  size_t bytes;
+};
+
+std::vector<CkptArray> ckpt_arrays(const Cube& cb, const fhs_iterate& a) {
+  const size_t img = (size_t)cb.L * cb.n1 * cb.n2 * 4, Q = (size_t)cb.Qy * cb.Qx;
+  return {{a.X, img}, {a.Xcheck, img}, {a.state.W, (size_t)cb.L * cb.sara.I * 4}, {a.state.theta, (size_t)cb.sara.I * 4},
+          {a.state.P, (size_t)cb.L * cb.n_facet_pix * 4}, {a.state.theta_bar, Q * cb.L * 4},
+          {a.state.v, (size_t)cb.n_vis * 8}, {a.state.u_prev, (size_t)cb.n_vis * 8}};
+}
+
+std::vector<int64_t> ckpt_shape(const Cube& cb) {
+  return {cb.n1, cb.n2, cb.L, cb.B, cb.Qy, cb.Qx, cb.n_vis, cb.sara.I, cb.n_facet_pix, cb.n_sub};
+}
+
+std::vector<double> ckpt_params(const Cube& cb) {
+  std::vector<double> p{cb.tau, cb.zeta, cb.kappa, cb.mu};
+  p.insert(p.end(), cb.eta.begin(), cb.eta.end());
+  p.insert(p.end(), cb.mu_bar.begin(), cb.mu_bar.end());
+  p.insert(p.end(), cb.eps.begin(), cb.eps.end());
+  return p;
+}
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) fclose(f);
+  }
+};
+
+void check_iterates(fhs_ctx* ctx, const fhs_iterate* it) {
+  FHS_REQUIRE(it, FHS_ERR_INVALID_ARG, "NULL iterates");
+  for (int c = 0; c < (int)ctx->cubes.size(); ++c) {
+    const fhs_iterate& a = it[c];
+    FHS_REQUIRE(a.X && a.Xcheck && a.state.W && a.state.theta && a.state.P && a.state.theta_bar && a.state.v &&
+                    a.state.u_prev,
+                FHS_ERR_INVALID_ARG, "NULL array in fhs_iterate");
+  }
+}
+}  // namespace
+
 // ====================================================================== C ABI
 extern "C" {
 
@@ -843,6 +911,7 @@ fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, 
   if (!cubes || ncubes < 1) { g_create_err = "need at least one cube"; return FHS_ERR_INVALID_ARG; }
   fhs_ctx* ctx = new fhs_ctx();
   ctx->stream = (cudaStream_t)stream;
+  g_alloc_used = 0;
   try {
     upload_kb_poly(kb_poly());
     Filters filt;
@@ -1267,6 +1336,119 @@ fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, d
 }
 
 uint64_t fhs_kernel_launches(void) { return g_launches.load(); }
+
+fhs_status fhs_checkpoint_save(fhs_ctx* ctx, const fhs_iterate* it, const char* path) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(path, FHS_ERR_INVALID_ARG, "NULL path");
+    check_iterates(ctx, it);
+    FileCloser fc{fopen(path, "wb")};
+    FHS_REQUIRE(fc.f, FHS_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
+    FHS_CUDA(cudaStreamSynchronize(ctx->stream));
+    Fnv h;
+    auto put = [&](const void* p, size_t n, bool hash) {
+      FHS_REQUIRE(fwrite(p, 1, n, fc.f) == n, FHS_ERR_INVALID_ARG, "checkpoint write failed");
+      if (hash) h.add(p, n);
+    };
+    put(kCkptMagic, sizeof(kCkptMagic), false);
+    const int64_t nc = (int64_t)ctx->cubes.size();
+    put(&nc, sizeof(nc), true);
+    for (const Cube& cb : ctx->cubes) {
+      const std::vector<int64_t> shp = ckpt_shape(cb);
+      const std::vector<double> prm = ckpt_params(cb);
+      put(shp.data(), shp.size() * 8, true);
+      put(prm.data(), prm.size() * 8, true);
+    }
+    std::vector<unsigned char> buf(kCkptChunk);
+    for (int c = 0; c < (int)nc; ++c)
+      for (const CkptArray& a : ckpt_arrays(ctx->cubes[c], it[c]))
+        for (size_t o = 0; o < a.bytes; o += kCkptChunk) {
+          const size_t n = std::min(kCkptChunk, a.bytes - o);
+          FHS_CUDA(cudaMemcpy(buf.data(), (const char*)a.dev + o, n, cudaMemcpyDeviceToHost));
+          put(buf.data(), n, true);
+        }
+    put(&h.h, sizeof(h.h), false);
+  });
+}
+
+fhs_status fhs_checkpoint_load(fhs_ctx* ctx, const fhs_iterate* it, const char* path) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(path, FHS_ERR_INVALID_ARG, "NULL path");
+    check_iterates(ctx, it);
+    FileCloser fc{fopen(path, "rb")};
+    FHS_REQUIRE(fc.f, FHS_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    auto get = [&](void* p, size_t n) {
+      FHS_REQUIRE(fread(p, 1, n, fc.f) == n, FHS_ERR_INVALID_ARG, "checkpoint truncated");
+    };
+    char magic[8];
+    get(magic, 8);
+    FHS_REQUIRE(memcmp(magic, kCkptMagic, 8) == 0, FHS_ERR_INVALID_ARG, "not a checkpoint of this library");
+    // pass 1: the hash over the whole payload, before anything is changed
+    const long start = ftell(fc.f);
+    FHS_REQUIRE(fseek(fc.f, 0, SEEK_END) == 0, FHS_ERR_INVALID_ARG, "checkpoint not seekable");
+    const long end = ftell(fc.f);
+    FHS_REQUIRE(end - start >= 16, FHS_ERR_INVALID_ARG, "checkpoint truncated");
+    fseek(fc.f, start, SEEK_SET);
+    std::vector<unsigned char> buf(kCkptChunk);
+    Fnv h;
+    for (long left = end - start - 8; left > 0;) {
+      const size_t n = (size_t)std::min<long>(left, (long)kCkptChunk);
+      get(buf.data(), n);
+      h.add(buf.data(), n);
+      left -= (long)n;
+    }
+    uint64_t stored = 0;
+    get(&stored, 8);
+    FHS_REQUIRE(stored == h.h, FHS_ERR_INVALID_ARG, "checkpoint corrupt (hash mismatch)");
+    // pass 2: shapes must match the context, then parameters and arrays
+    fseek(fc.f, start, SEEK_SET);
+    int64_t nc = 0;
+    get(&nc, 8);
+    FHS_REQUIRE(nc == (int64_t)ctx->cubes.size(), FHS_ERR_INVALID_ARG, "checkpoint has another number of cubes");
+    std::vector<std::vector<double>> prms;
+    for (Cube& cb : ctx->cubes) {
+      std::vector<int64_t> shp(ckpt_shape(cb).size());
+      get(shp.data(), shp.size() * 8);
+      std::vector<int64_t> mine = ckpt_shape(cb);
+      mine.back() = shp.back();     // n_sub may differ: the caller sets the preconditioner
+      FHS_REQUIRE(shp == mine, FHS_ERR_INVALID_ARG, "checkpoint of a cube of another shape");
+      std::vector<double> prm(ckpt_params(cb).size());
+      get(prm.data(), prm.size() * 8);
+      prms.push_back(prm);
+    }
+    for (int c = 0; c < (int)nc; ++c)
+      for (const CkptArray& a : ckpt_arrays(ctx->cubes[c], it[c]))
+        for (size_t o = 0; o < a.bytes; o += kCkptChunk) {
+          const size_t n = std::min(kCkptChunk, a.bytes - o);
+          get(buf.data(), n);
+          FHS_CUDA(cudaMemcpy((char*)a.dev + o, buf.data(), n, cudaMemcpyHostToDevice));
+        }
+    for (int c = 0; c < (int)nc; ++c) {
+      Cube& cb = ctx->cubes[c];
+      const std::vector<double>& p = prms[c];
+      const int L = cb.L, Q = cb.Qy * cb.Qx, LB = cb.L * cb.B;
+      cb.tau = p[0]; cb.zeta = p[1]; cb.kappa = p[2]; cb.mu = p[3];
+      cb.eta.assign(p.begin() + 4, p.begin() + 4 + L);
+      cb.mu_bar.assign(p.begin() + 4 + L, p.begin() + 4 + L + Q);
+      cb.eps.assign(p.begin() + 4 + L + Q, p.begin() + 4 + L + Q + LB);
+      std::vector<float> eta_f(cb.eta.begin(), cb.eta.end()), mub_f(cb.mu_bar.begin(), cb.mu_bar.end());
+      upload(cb.d_eps, cb.eps.data(), cb.eps.size(), ctx->stream);
+      upload(cb.d_eta, eta_f.data(), eta_f.size(), ctx->stream);
+      upload(cb.d_mubar, mub_f.data(), mub_f.size(), ctx->stream);
+    }
+    FHS_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->param_version++;
+  });
+}
+
+fhs_status fhs_set_wait_limit(int64_t spins) {
+  if (spins < -1) return FHS_ERR_INVALID_ARG;
+  return set_wait_first((long long)spins) == cudaSuccess ? FHS_OK : FHS_ERR_CUDA;
+}
+
+fhs_status fhs_set_alloc_limit(uint64_t bytes) {
+  g_alloc_limit.store(bytes);
+  return FHS_OK;
+}
 
 fhs_status fhs_set_kernel_timer(fhs_ctx* ctx, int32_t kernel) {
   return guarded(ctx, [&] {

@@ -23,6 +23,7 @@
 namespace fhs {
 // Device status word: bits set by bounded waits that gave up (read by the host).
 __device__ unsigned int g_dev_status = 0;
+__device__ long long g_wait_first = 0;   // first phase of the bounded waits (0: default)
 }  // namespace fhs
 
 #include "tma.cuh"
@@ -1105,6 +1106,12 @@ void encode_degrid_maps(fhs_ctx* ctx) {
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     cb.tma = (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS);
   }
+}
+
+cudaError_t set_wait_first(long long spins) {
+  cudaError_t e = cudaMemcpyToSymbol(g_wait_first, &spins, sizeof(spins));
+  if (e == cudaSuccess) e = set_gram_wait_first(spins);
+  return e;
 }
 
 unsigned read_device_status(bool clear) {

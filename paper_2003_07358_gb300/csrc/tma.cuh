@@ -16,7 +16,10 @@ namespace fhs {
 constexpr unsigned kDevTimeoutTMA = 1u;   // device status bit: a TMA wait gave up
 constexpr long long kTmaSpinLimit = 1ll << 22;
 
-// The including translation unit defines `__device__ unsigned int g_dev_status`.
+// The including translation unit defines `__device__ unsigned int g_dev_status` and
+// `__device__ long long g_wait_first`: the length of the first phase of the bounded
+// waits (0: kTmaSpinLimit; negative: no polls, the wait gives up at once), changed only
+// by the fault-injection hook fhs_set_wait_limit.
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -43,7 +46,8 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
 // Bounded wait for phase `parity` of the barrier; false (and the status bit) on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   const unsigned a = smem_addr(bar);
-  for (long long it = 0; it < kTmaSpinLimit; ++it) {
+  const long long first = g_wait_first > 0 ? g_wait_first : (g_wait_first < 0 ? 0 : kTmaSpinLimit);
+  for (long long it = 0; it < first; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -27,7 +27,8 @@ SYMBOLS = [
     "fhs_proj_l2ball_blocks", "fhs_reweight", "fhs_pdfb_iter", "fhs_set_params", "fhs_kernel_launches",
     "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path", "fhs_set_kernel_timer",
     "fhs_kernel_timer_read", "fhs_solve", "fhs_heuristic_params", "fhs_set_preconditioning",
-    "fhs_pdfb_iter_host",
+    "fhs_pdfb_iter_host", "fhs_set_wait_limit", "fhs_set_alloc_limit",
+    "fhs_checkpoint_save", "fhs_checkpoint_load",
 ]
 MAX_SOLVE_CYCLES = 32
 FHS_PATH = {"fast": 0, "plain": 1}
@@ -119,6 +120,10 @@ def load(path: str = LIB_PATH):
         "fhs_solve": ([vp, C.POINTER(fhs_iterate), C.POINTER(fhs_solve_params), C.POINTER(fhs_solve_report)], i32),
         "fhs_heuristic_params": ([vp, i32, dp, i32, C.c_double, dp, dp, dp, dp], i32),
         "fhs_set_preconditioning": ([vp, i32, i32, C.POINTER(C.c_float)], i32),
+        "fhs_set_wait_limit": ([C.c_int64], i32),
+        "fhs_checkpoint_save": ([vp, C.POINTER(fhs_iterate), C.c_char_p], i32),
+        "fhs_checkpoint_load": ([vp, C.POINTER(fhs_iterate), C.c_char_p], i32),
+        "fhs_set_alloc_limit": ([C.c_uint64], i32),
         "fhs_pdfb_iter_host": ([vp, C.POINTER(fhs_iterate), C.POINTER(vp), C.POINTER(vp), i32,
                                 C.POINTER(fhs_iter_stats)], i32),
     }
@@ -136,6 +141,20 @@ def _ptr(t) -> int | None:
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("libfhs takes contiguous CUDA tensors")
     return t.data_ptr()
+
+
+def fhs_set_wait_limit(spins: int) -> None:
+    """Fault-injection hook: first phase of the bounded device-side waits (0: default)."""
+    rc = load().fhs_set_wait_limit(spins)
+    if rc != 0:
+        raise FhsError(rc, "fhs_set_wait_limit")
+
+
+def fhs_set_alloc_limit(nbytes: int) -> None:
+    """Fault-injection hook: cap on the device bytes one context may allocate (0: none)."""
+    rc = load().fhs_set_alloc_limit(nbytes)
+    if rc != 0:
+        raise FhsError(rc, "fhs_set_alloc_limit")
 
 
 def _host_ptr(a, dtype) -> int:
@@ -395,6 +414,12 @@ class Context:
         if not want_stats:
             return None
         return [{"xi": s.xi, "res_norm": s.res_norm, "eps_norm": s.eps_norm} for s in stats]
+
+    def fhs_checkpoint_save(self, iterates: list[dict], path: str):
+        self._check(self.lib.fhs_checkpoint_save(self.h, self._iterates(iterates), os.fsencode(path)))
+
+    def fhs_checkpoint_load(self, iterates: list[dict], path: str):
+        self._check(self.lib.fhs_checkpoint_load(self.h, self._iterates(iterates), os.fsencode(path)))
 
     def fhs_set_params(self, cube, tau, zeta, kappa, eta, mu, mu_bar, eps):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (eta, mu_bar, eps)]
