@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "CubeSpec", "WORKLOADS", "workload", "frequencies", "subcube_channels",
     "sky_sources", "render_channel", "sky_cube", "base_uv", "channel_uv", "radial_blocks", "unit_noise",
-    "ProblemInputs", "make_inputs",
+    "ProblemInputs", "make_inputs", "DdeInputs", "dde_inputs",
 ]
 
 
@@ -232,6 +232,7 @@ class ProblemInputs:
     M_lb: np.ndarray
     noise: np.ndarray
     chans: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=int))
+    perm: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int64))   # block order of the reference points
 
 
 def make_inputs(spec: CubeSpec, cube: int = 0, with_noise: bool = True) -> ProblemInputs:
@@ -257,4 +258,62 @@ def make_inputs(spec: CubeSpec, cube: int = 0, with_noise: bool = True) -> Probl
     else:
         noise = np.zeros(Lc * spec.M, dtype=np.complex128)
     return ProblemInputs(spec=spec, cube=cube, x_true=x, uv=uv, M_lb=M_lb,
-                         noise=noise, chans=chans)
+                         noise=noise, chans=chans, perm=perm)
+
+
+@dataclass
+class DdeInputs:
+    """Synthetic direction-dependent effects of one sub-cube (Section 2.1, after Eq. 1).
+
+    Each antenna a and channel l has a pattern D_{a,l}(p) with an S_a x S_a Fourier-domain
+    representation d_{a,l} on the lattice of the 2x oversampled grid (centre coefficient 1,
+    the other coefficients small, decaying away from the centre).  Visibility m of
+    baseline (a, b) sees the sky multiplied by D_a conj(D_b), whose representation is the
+    S_d x S_d = (2 S_a - 1)^2 convolution of d_a with d~_b[j] = conj(d_b[-j]).
+
+    kern : [Lc * n_bl][S_d][S_d] complex128, kernel of (channel i of the sub-cube,
+           baseline k) at index i * n_bl + k; first index along grid rows (v)
+    kidx : [Lc * M] int32, kernel of each visibility, in the order of ProblemInputs.uv
+    """
+    kern: np.ndarray
+    kidx: np.ndarray
+    n_ant: int
+    S_a: int
+
+
+def dde_inputs(inp: ProblemInputs, n_ant: int = 8, S_a: int = 5, amp: float = 0.05) -> DdeInputs:
+    """DDE kernels and per-visibility kernel indices for `inp`.
+
+    Draw order with rng = default_rng(spec.seed + 7919): the baseline of every reference
+    visibility (integers in [0, n_bl)), then for every channel of the cube in global
+    order and every antenna, S_a x S_a x 2 standard normals (real, imaginary parts),
+    scaled by amp * exp(-|j|^2 / 2); the centre coefficient is then set to 1.
+    """
+    spec = inp.spec
+    rng = np.random.default_rng(spec.seed + 7919)
+    pairs = [(a, b) for a in range(n_ant) for b in range(a + 1, n_ant)]
+    n_bl = len(pairs)
+    bl = rng.integers(0, n_bl, size=spec.M)
+    R = S_a // 2
+    j = np.arange(-R, R + 1)
+    taper = amp * np.exp(-(j[:, None] ** 2 + j[None, :] ** 2) / 2.0)
+    d_all = {}
+    for l in range(spec.L):
+        d = rng.standard_normal((n_ant, S_a, S_a, 2))
+        d = (d[..., 0] + 1j * d[..., 1]) * taper
+        d[:, R, R] = 1.0
+        d_all[l] = d
+    S_d = 2 * S_a - 1
+    kern = np.zeros((inp.chans.size * n_bl, S_d, S_d), dtype=np.complex128)
+    for i, l in enumerate(inp.chans):
+        d = d_all[int(l)]
+        for k, (a, b) in enumerate(pairs):
+            db = np.conj(d[b][::-1, ::-1])                          # d~_b[j] = conj(d_b[-j])
+            out = kern[i * n_bl + k]
+            for r in range(S_a):
+                for c in range(S_a):
+                    out[r:r + S_a, c:c + S_a] += d[a][r, c] * db
+    # visibilities are block-ordered in ProblemInputs (inp.perm)
+    perm = inp.perm
+    kidx = np.concatenate([i * n_bl + bl[perm] for i in range(inp.chans.size)]).astype(np.int32)
+    return DdeInputs(kern=kern, kidx=kidx, n_ant=n_ant, S_a=S_a)

@@ -22,23 +22,25 @@ from scipy.special import gammaln
 
 from . import facets as fc
 from . import nufft as nu
+from . import dde as dd
 from . import prox as px
 from . import wavelets as wv
 
 
 # ------------------------------------------------------------------ parameters
 def op_norm_sq(uv: np.ndarray, n1: int, n2: int, x0: np.ndarray, max_iter: int = 100,
-               rel_tol: float = 1e-4, U: np.ndarray | None = None) -> float:
+               rel_tol: float = 1e-4, U: np.ndarray | None = None, dde_k=None) -> float:
     """||Phi||_S^2 on real images by the power method on Re(Phi^dagger Phi)
     (footnote of Section 2.3.1: relative variation below 1e-4, at most 100 iterations);
-    with a preconditioner, ||U^1/2 Phi||_S^2 from Re(Phi^dagger U Phi) (Section 3.2)."""
+    with a preconditioner, ||U^1/2 Phi||_S^2 from Re(Phi^dagger U Phi) (Section 3.2);
+    dde_k = (kern, kidx of these visibilities): the DDE-extended Phi (Section 2.1)."""
     x = x0 / np.linalg.norm(x0)
     val = 0.0
     for _ in range(max_iter):
-        m = nu.measure(x, uv)
+        m = nu.measure(x, uv) if dde_k is None else dd.measure(x, uv, dde_k[0], dde_k[1])
         if U is not None:
             m = U * m
-        y = nu.adjoint(m, uv, n1, n2).real
+        y = (nu.adjoint(m, uv, n1, n2) if dde_k is None else dd.adjoint(m, uv, dde_k[0], dde_k[1], n1, n2)).real
         new = np.linalg.norm(y)
         x = y / new
         if val > 0 and abs(new - val) / new < rel_tol:
@@ -120,6 +122,7 @@ class Problem:
     facets: list = field(default_factory=list)
     U: np.ndarray | None = None     # [sum M] diagonal preconditioner (None: U = I)
     n_sub: int = 20                 # forward-backward sub-iterations of the U-projection
+    dde: tuple | None = None        # (kern [n_kern][S_d][S_d], kidx [sum M]): DDE-extended G (Section 2.1)
 
     def __post_init__(self):
         if not self.facets:
@@ -172,10 +175,24 @@ def initial_state(prob: Problem, X0: np.ndarray | None = None) -> State:
                  theta_bar=np.ones((len(prob.facets), L)), v=np.zeros_like(prob.y), u_prev=u0)
 
 
+def measure_l(prob: Problem, x: np.ndarray, sl: slice) -> np.ndarray:
+    """Phi_l x for the visibilities sl of one channel (DDE-extended G when prob.dde is set)."""
+    if prob.dde is None:
+        return nu.measure(x, prob.uv[sl])
+    return dd.measure(x, prob.uv[sl], prob.dde[0], prob.dde[1][sl])
+
+
+def adjoint_l(prob: Problem, v: np.ndarray, sl: slice) -> np.ndarray:
+    """Phi_l^dagger v (complex image) for the visibilities sl of one channel."""
+    if prob.dde is None:
+        return nu.adjoint(v, prob.uv[sl], prob.n1, prob.n2)
+    return dd.adjoint(v, prob.uv[sl], prob.dde[0], prob.dde[1][sl], prob.n1, prob.n2)
+
+
 def measure_all(prob: Problem, X: np.ndarray) -> np.ndarray:
     out = np.zeros(prob.uv.shape[0], dtype=np.complex128)
     for l, sl in enumerate(prob.channel_slices()):
-        out[sl] = nu.measure(X[l], prob.uv[sl])
+        out[sl] = measure_l(prob, X[l], sl)
     return out
 
 
@@ -218,7 +235,7 @@ def data_step(prob: Problem, X: np.ndarray, v: np.ndarray, u_prev: np.ndarray):
         res[l, b] = np.linalg.norm(prob.y[sl] - u[sl])
     A = np.zeros_like(X)
     for l, sl in enumerate(prob.channel_slices()):
-        A[l] = prob.eta[l] * nu.adjoint(vn[sl], prob.uv[sl], prob.n1, prob.n2).real
+        A[l] = prob.eta[l] * adjoint_l(prob, vn[sl], sl).real
     return vn, u, res, A
 
 
@@ -347,4 +364,18 @@ def precondition(prob: Problem, n_sub: int = 20, power_iters: int = 100, seed: i
         eta[l] = 1.0 / op_norm_sq(prob.uv[sl], prob.n1, prob.n2, rng.standard_normal((prob.n1, prob.n2)),
                                   max_iter=power_iters, U=U[sl])
     prob.U, prob.n_sub, prob.eta = U, n_sub, eta
+    return prob
+
+
+def with_dde(prob: Problem, inp, dde_in, sigma: np.ndarray, power_iters: int = 100, seed: int = 9) -> Problem:
+    """The DDE-extended measurement model of Section 2.1 on prob (in place): G_l rows are
+    the Kaiser-Bessel kernel convolved with each visibility's DDE kernel; the data become
+    y = Phi_l x_true + sigma_l n with the same unit noise, and eta_l = 1 / ||Phi_l||_S^2
+    of the extended operator."""
+    rng = np.random.default_rng(seed)
+    prob.dde = (np.asarray(dde_in.kern), np.asarray(dde_in.kidx))
+    for l, sl in enumerate(prob.channel_slices()):
+        prob.y[sl] = measure_l(prob, inp.x_true[l], sl) + sigma[l] * inp.noise[sl]
+        prob.eta[l] = 1.0 / op_norm_sq(prob.uv[sl], prob.n1, prob.n2, rng.standard_normal((prob.n1, prob.n2)),
+                                       max_iter=power_iters, dde_k=(prob.dde[0], prob.dde[1][sl]))
     return prob
