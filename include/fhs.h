@@ -222,6 +222,26 @@ fhs_status fhs_heuristic_params(fhs_ctx* ctx, int32_t cube, const double* sigma,
  * Errors: INVALID_ARG, OOM, CUDA. */
 fhs_status fhs_set_preconditioning(fhs_ctx* ctx, int32_t cube, int32_t n_sub, const float* U);
 
+/* DDE-extended de-gridding kernels of a cube (Section 2.1, after Eq. 1): row m of G_l
+ * becomes the Kaiser-Bessel kernel convolved with the visibility's compact Fourier-
+ * domain DDE kernel K_m, g_m[k] = sum_j K_m[j] phi(t_r - (k_r - j_r)) phi(t_c - (k_c -
+ * j_c)) for j in [-R, R]^2, a (7 + 2R) x (7 + 2R) footprint (15 x 15 for S_d = 9).  The
+ * visibilities then model the sky multiplied by the pattern a_m(p) = sum_j K_m[j]
+ * exp(-2 pi i (j_r p_r / K1 + j_c p_c / K2)).  Every operator of the cube follows:
+ * fhs_measure, fhs_adjoint (conjugated kernels), fhs_pdfb_iter, fhs_solve,
+ * fhs_opnorm_sq and fhs_heuristic_params (set eta again afterwards).
+ *  S_d    : kernel side, odd in [1, 9]; 0 returns to the plain 7 x 7 rows;
+ *  n_kern : number of kernels (>= 1);
+ *  kern   : host, complex64 as float pairs, [n_kern][S_d][S_d], first index along grid
+ *           rows (the v axis, j_r = index - R), second along columns (u);
+ *  kidx   : host [n_vis] int32 in the caller's visibility order, kernel of each
+ *           visibility, in [0, n_kern).
+ * The library copies both; gridding stays bitwise deterministic.  Synchronising.
+ * Errors: INVALID_ARG (S_d, an index out of range, a non-finite coefficient),
+ * UNSUPPORTED (footprint wider than a grid tile, K < 16), OOM, CUDA. */
+fhs_status fhs_set_dde(fhs_ctx* ctx, int32_t cube, int32_t S_d, int32_t n_kern, const float* kern,
+                       const int32_t* kidx);
+
 /* Replace the algorithm parameters of a cube (same meaning and host arrays as in
  * fhs_cube_desc: eta [L], mu_bar [Qy*Qx], eps [L*B]).  Lets a caller compute
  * eta = 1/||Phi_l||^2 with fhs_opnorm_sq and the noise-based heuristics

@@ -15,6 +15,7 @@ namespace fhs {
 constexpr int kTaps = 7;          // Kaiser-Bessel support J
 constexpr int kPolyDeg = 11;      // per-tap polynomial degree of the kernel fit
 constexpr int kGridTile = 64;     // gridder tile side (cells)
+constexpr int kDdeMaxR = 4;       // DDE kernels up to 9 x 9 (extended footprints up to 15 x 15)
 constexpr int kLevels = 4;        // SARA decomposition levels
 constexpr int kMaxB = 16;         // data blocks per channel
 constexpr int kMaxL = 64;         // channels per cube
@@ -78,6 +79,15 @@ struct Cube {
   // (0: U = I, Euclidean projections), U per visibility (internal order), gamma per block
   int n_sub = 0;
   float* d_U = nullptr;                      // [n_vis]
+  // DDE-extended G (Section 2.1): kernel half-width R (-1: plain Kaiser-Bessel rows),
+  // kernels [n_kern][2R+1][2R+1], kernel of each visibility (internal order), per kernel
+  // sum of |Re| + |Im| (rounded up), per (channel, tile) largest extended-footprint count
+  int dde_R = -1;
+  int dde_nkern = 0;
+  float2* d_dde_kern = nullptr;
+  int32_t* d_dde_idx = nullptr;
+  float* d_dde_l1 = nullptr;
+  int* d_dde_ncmax = nullptr;
   float* d_gamma = nullptr;                  // [L*B] 1 / max U of the block
   float* d_eta = nullptr;                    // [L]
   float* d_mubar = nullptr;                  // [Q]
@@ -177,6 +187,12 @@ int host_first_tap(float om, int K);
 void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write,
                  float2* grid, cudaStream_t st);
 void launch_grid_count(const Cube& cb, cudaStream_t st);
+void launch_degrid_dde(const Cube& cb, const float2* grid, float2* out, cudaStream_t st);
+void launch_degrid_pdfb_dde(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
+                            float2* u_prev, double* partials, int nparts, cudaStream_t st);
+void launch_grid_dde(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write, float2* grid,
+                     cudaStream_t st);
+void launch_grid_dde_count(const Cube& cb, cudaStream_t st);
 void launch_l2ball_partials(const Cube& cb, const float2* z, const float2* y, float2* d,
                             double* partials, int nparts, cudaStream_t st);
 void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, float2* v, cudaStream_t st);

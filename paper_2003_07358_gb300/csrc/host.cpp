@@ -509,7 +509,8 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
 
 void free_cube(Cube& cb) {
   void* ps[] = {cb.d_uv, cb.d_blk, cb.d_perm, cb.d_vis_off, cb.d_tile_off, cb.d_facets, cb.d_win, cb.d_win64, cb.d_tile_of,
-                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar, cb.d_ncmax, cb.d_M_lb, cb.d_U, cb.d_gamma};
+                cb.d_scale_r, cb.d_scale_c, cb.d_eps, cb.d_eta, cb.d_mubar, cb.d_ncmax, cb.d_M_lb, cb.d_U, cb.d_gamma,
+                cb.d_dde_kern, cb.d_dde_idx, cb.d_dde_l1, cb.d_dde_ncmax};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -649,7 +650,14 @@ void pdfb_iteration_cube(fhs_ctx* ctx, int c, const fhs_iterate& a) {
     // preconditioned duals (Section 3.2): the degridder forms d = U^-1 v + Phi x_check - y
     if (cb.n_sub > 0) launch_vis_scale((float2*)a.state.v, cb.d_U, cb.n_vis, true, st);
     int np;
-    if (use_fast(ctx, cb)) {
+    if (cb.dde_R >= 0) {
+      // DDE-extended rows (Section 2.1): the warp-per-visibility de-gridder
+      np = degrid_parts(cb);
+      timer_mark(ctx, FHS_TIMER_DEGRID, 2 * c);
+      launch_degrid_pdfb_dde(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
+                             (float2*)a.state.u_prev, ctx->s.red, np, st);
+      timer_mark(ctx, FHS_TIMER_DEGRID, 2 * c + 1);
+    } else if (use_fast(ctx, cb)) {
       np = degrid_tiled_parts(cb);
       timer_mark(ctx, FHS_TIMER_DEGRID, 2 * c);
       launch_degrid_pdfb_tiled(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
@@ -1306,6 +1314,58 @@ fhs_status fhs_set_preconditioning(fhs_ctx* ctx, int32_t cube, int32_t n_sub, co
     upload(cb.d_gamma, gamma.data(), gamma.size(), st);
     FHS_CUDA(cudaStreamSynchronize(st));
     cb.n_sub = n_sub;
+  });
+}
+
+fhs_status fhs_set_dde(fhs_ctx* ctx, int32_t cube, int32_t S_d, int32_t n_kern, const float* kern,
+                       const int32_t* kidx) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(cube >= 0 && cube < (int32_t)ctx->cubes.size(), FHS_ERR_INVALID_ARG, "cube index out of range");
+    FHS_REQUIRE(S_d == 0 || (S_d >= 1 && S_d <= 2 * kDdeMaxR + 1 && (S_d & 1)), FHS_ERR_INVALID_ARG,
+                "S_d must be 0 or odd in [1, 9]");
+    Cube& cb = ctx->cubes[cube];
+    cudaStream_t st = ctx->stream;
+    FHS_CUDA(cudaStreamSynchronize(st));
+    ctx->param_version++;
+    if (S_d == 0) {
+      cb.dde_R = -1;
+      return;
+    }
+    FHS_REQUIRE(kern && kidx && n_kern >= 1, FHS_ERR_INVALID_ARG, "kernels and indices are required");
+    FHS_REQUIRE(kTaps + S_d - 1 <= cb.tile, FHS_ERR_UNSUPPORTED, "extended footprint wider than a grid tile");
+    const int sd2 = S_d * S_d;
+    std::vector<float> l1(n_kern);
+    for (int k = 0; k < n_kern; ++k) {
+      double a = 0.0;
+      for (int j = 0; j < 2 * sd2; ++j) {
+        const float x = kern[(size_t)k * 2 * sd2 + j];
+        FHS_REQUIRE(std::isfinite(x), FHS_ERR_INVALID_ARG, "non-finite DDE kernel coefficient");
+        a += fabs((double)x);
+      }
+      l1[k] = (float)(a * (1.0 + 1.0 / (1 << 20)));     // rounded up: a bound of the tap values
+    }
+    const int64_t n = cb.n_vis;
+    std::vector<int32_t> idx(n);
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t k = kidx[cb.perm_host[i]];
+      FHS_REQUIRE(k >= 0 && k < n_kern, FHS_ERR_INVALID_ARG, "DDE kernel index out of range");
+      idx[i] = k;
+    }
+    if (cb.d_dde_kern) { cudaFree(cb.d_dde_kern); cb.d_dde_kern = nullptr; }
+    if (cb.d_dde_l1) { cudaFree(cb.d_dde_l1); cb.d_dde_l1 = nullptr; }
+    cb.d_dde_kern = dalloc<float2>((size_t)n_kern * sd2);
+    cb.d_dde_l1 = dalloc<float>(n_kern);
+    if (!cb.d_dde_idx) cb.d_dde_idx = dalloc<int32_t>(n ? n : 1);
+    if (!cb.d_dde_ncmax) cb.d_dde_ncmax = dalloc<int>((size_t)cb.L * cb.ntile_r * cb.ntile_c);
+    upload(cb.d_dde_kern, reinterpret_cast<const float2*>(kern), (size_t)n_kern * sd2, st);
+    upload(cb.d_dde_l1, l1.data(), l1.size(), st);
+    if (n) upload(cb.d_dde_idx, idx.data(), idx.size(), st);
+    cb.dde_R = (S_d - 1) / 2;
+    cb.dde_nkern = n_kern;
+    // the extended footprints covering each cell of a tile fix its fixed-point scale
+    launch_grid_dde_count(cb, st);
+    FHS_CUDA(cudaGetLastError());
+    FHS_CUDA(cudaStreamSynchronize(st));
   });
 }
 

@@ -1125,6 +1125,10 @@ unsigned read_device_status(bool clear) {
 }
 
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st) {
+  if (cb.dde_R >= 0) {
+    launch_degrid_dde(cb, grid, out, st);
+    return;
+  }
   if (tiled) {
     dim3 grd(degrid_tiled_parts(cb), cb.L);
     k_degrid_tiled<0><<<grd, 256, degrid_tiled_smem(cb), st>>>(grid, cb.d_uv, cb.d_tile_off, cb.d_vis_off,
@@ -1196,6 +1200,10 @@ void launch_l2ball_scale(const Cube& cb, const float2* d, const float* scale, fl
 
 void launch_grid(const Cube& cb, const float2* vals, const float* blk_scale, float2* v_write, float2* grid,
                  cudaStream_t st) {
+  if (cb.dde_R >= 0) {
+    launch_grid_dde(cb, vals, blk_scale, v_write, grid, st);
+    return;
+  }
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_grid<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024); attr = true; }
   dim3 grd(cb.ntile_r * cb.ntile_c, cb.L);
@@ -1252,3 +1260,5 @@ int host_first_tap(float om, int K) {
 }
 
 }  // namespace fhs
+
+#include "dde.cuh"

@@ -28,7 +28,7 @@ SYMBOLS = [
     "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path", "fhs_set_kernel_timer",
     "fhs_kernel_timer_read", "fhs_solve", "fhs_heuristic_params", "fhs_set_preconditioning",
     "fhs_pdfb_iter_host", "fhs_set_wait_limit", "fhs_set_alloc_limit",
-    "fhs_checkpoint_save", "fhs_checkpoint_load",
+    "fhs_checkpoint_save", "fhs_checkpoint_load", "fhs_set_dde",
 ]
 MAX_SOLVE_CYCLES = 32
 FHS_PATH = {"fast": 0, "plain": 1}
@@ -124,6 +124,7 @@ def load(path: str = LIB_PATH):
         "fhs_checkpoint_save": ([vp, C.POINTER(fhs_iterate), C.c_char_p], i32),
         "fhs_checkpoint_load": ([vp, C.POINTER(fhs_iterate), C.c_char_p], i32),
         "fhs_set_alloc_limit": ([C.c_uint64], i32),
+        "fhs_set_dde": ([vp, i32, i32, i32, C.POINTER(C.c_float), C.POINTER(C.c_int32)], i32),
         "fhs_pdfb_iter_host": ([vp, C.POINTER(fhs_iterate), C.POINTER(vp), C.POINTER(vp), i32,
                                 C.POINTER(fhs_iter_stats)], i32),
     }
@@ -400,6 +401,23 @@ class Context:
         if u.size != self.sizes(cube)["n_vis"]:
             raise ValueError("U must have one entry per visibility of the cube")
         self._check(self.lib.fhs_set_preconditioning(self.h, cube, n_sub, u.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def fhs_set_dde(self, cube, kern=None, kidx=None):
+        """DDE-extended de-gridding kernels: kern [n_kern][S_d][S_d] complex (first index
+        along grid rows), kidx [n_vis] kernel of each visibility in the caller's order;
+        kern None returns to the plain Kaiser-Bessel rows."""
+        if kern is None:
+            self._check(self.lib.fhs_set_dde(self.h, cube, 0, 0, None, None))
+            return
+        k = np.ascontiguousarray(kern, dtype=np.complex64)
+        if k.ndim != 3 or k.shape[1] != k.shape[2]:
+            raise ValueError("kern must be [n_kern][S_d][S_d]")
+        idx = np.ascontiguousarray(kidx, dtype=np.int32).ravel()
+        if idx.size != self.sizes(cube)["n_vis"]:
+            raise ValueError("kidx must have one entry per visibility of the cube")
+        kf = k.view(np.float32)
+        self._check(self.lib.fhs_set_dde(self.h, cube, k.shape[1], k.shape[0], kf.ctypes.data_as(C.POINTER(C.c_float)),
+                                         idx.ctypes.data_as(C.POINTER(C.c_int32))))
 
     def fhs_pdfb_iter_host(self, iterates: list[dict], y_host: list, X_host: list, n_iter: int,
                            want_stats: bool = True):
