@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-ops", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-snr-gap", action="store_true")
+    ap.add_argument("--no-dde", action="store_true")
     ap.add_argument("--dry-run", action="store_true",
                     help="set up the ranks (gloo, CPU) and print each rank's sub-cube seed offset, nothing else")
     return ap.parse_args()
@@ -208,6 +209,81 @@ def setup(spec: fs.CubeSpec, torch, seed_offset: int, opnorm_iters: int, log):
     ctx.sync()
     log(f"data, parameters and state ready in {time.time() - t0:.1f} s")
     return ctx, iterates
+
+
+# --------------------------------------------- DDE-extended de-gridding (Section 2.1)
+DDE_WORKLOAD = "facet_slice"
+DDE_S_A = 5            # 5 x 5 per antenna -> 9 x 9 per baseline -> 15 x 15 footprints
+DDE_N_ANT = 27         # 351 baselines
+
+
+def dde_flops_per_vis(S_d: int) -> int:
+    """FP32 flops of one visibility in either direction (2 per FMA): column pass
+    F S_d x 7 complex-by-real, row pass S_d^2 x 7, kernel product S_d^2 complex."""
+    F = 7 + S_d - 1
+    return 2 * (14 * F * S_d + 14 * S_d * S_d + 4 * S_d * S_d)
+
+
+def dde_measurement(args, torch, log, sm_mhz) -> dict:
+    """Both DDE kernels inside PDFB iterations of the 1024^2 x 16 workload with 15 x 15
+    footprints, their ALU roofline (FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x
+    clock), and the oracle's de-gridding + gridding on a sample of the same rows."""
+    from oracle import dde as odde
+    spec = fs.workload(DDE_WORKLOAD)
+    ctx, its = setup(spec, torch, 0, 10, log)
+    rng = np.random.default_rng(spec.seed)
+    fs.sky_sources(spec, rng)
+    base = fs.base_uv(spec, rng)
+    perm = np.concatenate(fs.radial_blocks(base, spec.B))
+    chans = fs.subcube_channels(spec, 0)
+    shim = type("Inp", (), {"spec": spec, "chans": chans, "perm": perm})()
+    dd = fs.dde_inputs(shim, n_ant=DDE_N_ANT, S_a=DDE_S_A)
+    S_d = dd.kern.shape[1]
+    stream = ctx.stream
+
+    def timed_iters(k):
+        ctx.fhs_pdfb_iter(its, 1, want_stats=False)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            ctx.fhs_pdfb_iter(its, 1, want_stats=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    plain_ms = timed_iters(3)
+    ctx.fhs_set_dde(0, dd.kern, dd.kidx)
+    out = {"workload": spec.name, "kernel": f"{S_d}x{S_d} DDE kernels, {7 + S_d - 1}x{7 + S_d - 1} footprints",
+           "baselines": DDE_N_ANT * (DDE_N_ANT - 1) // 2, "visibilities_per_launch": int(spec.M * spec.Lc)}
+    for name in ("degrid", "grid"):
+        ctx.fhs_set_kernel_timer(name)
+        ms = timed_iters(3)
+        t, n = ctx.fhs_kernel_timer_read()
+        ctx.fhs_set_kernel_timer(None)
+        sec = t / n / 1000.0
+        flops = dde_flops_per_vis(S_d) * spec.M * spec.Lc
+        peak = 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+        ach = flops / sec / 1e12
+        out[name] = {"ms_per_launch": round(sec * 1e3, 3), "vis_per_s": round(spec.M * spec.Lc / sec, 1),
+                     "roofline": {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
+                                  "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                                  "peak_kind": "derived: FP32 FMA lanes x 2 x sampled SM clock"}}
+    out["iteration_ms"] = {"plain_rows": round(plain_ms, 3), "dde_rows": round(ms, 3)}
+    ctx.close()
+    # the oracle on a sample of the same rows (one channel, 4000 visibilities)
+    K = 2 * spec.n
+    g = np.random.default_rng(1).standard_normal((K, K)) + 0j
+    uvs = (base[perm[:4000]]).astype(np.float32).astype(np.float64)
+    kidx = dd.kidx[:4000]
+    t0 = time.perf_counter()
+    u = odde.degrid(g, uvs, dd.kern, kidx)
+    odde.grid_adjoint(u, uvs, dd.kern, kidx, K, K)
+    dt = time.perf_counter() - t0
+    out["oracle"] = {"vis_per_s_degrid_plus_grid": round(4000 / dt, 1), "cores": 1,
+                     "sample": "4000 visibilities of channel 0 on a 2048^2 grid, de-gridding then gridding"}
+    return out
 
 
 # ------------------------------------------------------- algorithmic bytes
@@ -580,6 +656,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_snr_gap:
         gaps = snr_gaps(torch, log)
 
+    dde_line = None
+    if rank == 0 and world == 1 and not args.no_dde:
+        dde_line = dde_measurement(args, torch, log, clocks.get("sm_mhz"))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = time.time()
@@ -605,7 +685,8 @@ def main():
                            "path": "FP32 fused kernels (FP64 reductions)",
                            "l2": "working set ~100 GB >> 129 MB L2; no flush"},
                 "roofline": roofline, "operators": ops, "cpu_baseline": cpu, "e2e": e2e,
-                "plain_fp32_path": plain, "snr_gap_vs_fp64": gaps, "clocks": clocks, "gpu_launches": launches}
+                "plain_fp32_path": plain, "snr_gap_vs_fp64": gaps, "dde_degridding": dde_line, "clocks": clocks,
+                "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
