@@ -346,6 +346,43 @@ fhs_status fhs_checkpoint_load(fhs_ctx* ctx, const fhs_iterate* it, const char* 
  * fhs_set_alloc_limit caps the device bytes the library allocates on the calling thread
  * from the start of each fhs_create (0: no cap); a request beyond it fails with
  * FHS_ERR_OOM.  Both apply process-wide. */
+/* ------------------------------------------------------------- autotuner */
+/* Per-shape launch choices of a cube, for the batching form (many cubes of different
+ * shapes, Section 2.4.1).  Each candidate is a kernel the library also runs untuned:
+ *  grid_tile        : side (cells) of the gridder / de-gridder tiles, 32 or 64; it
+ *                     fixes the internal visibility order, so it is chosen inside
+ *                     fhs_create from trial cubes over the first two channels;
+ *  degrid_tiled     : 1 tile-staged (TMA) de-gridder, 0 direct per-visibility one;
+ *  gram_tc          : 1 tcgen05 error-free facet Gram (L <= 32), 0 CUDA-core float-float;
+ *  sara_fast        : 1 fused SARA tiles, 0 separate analysis / dual / synthesis passes;
+ *  prox_ctas_per_sm : CTAs per SM of the fused l2,1 dual pass;
+ *  source           : 0 defaults (autotuning off), 1 measured, 2 read from the cache;
+ *  ms               : measured times (ms): [0] grid + de-grid with 32-cell tiles, [1] with
+ *                     64, [2] tile-staged de-grid, [3] direct, [4] tcgen05 Gram, [5]
+ *                     CUDA-core Gram, [6] SARA weights by separate passes, [7..9] fused
+ *                     with 4, 8, 16 CTAs per SM (0 where not measured). */
+typedef struct {
+  int32_t grid_tile;
+  int32_t degrid_tiled;
+  int32_t gram_tc;
+  int32_t sara_fast;
+  int32_t prox_ctas_per_sm;
+  int32_t source;
+  double ms[10];
+} fhs_tuning;
+
+/* Process-wide switch for the contexts created afterwards.  mode 0: defaults (tile 64,
+ * tile-staged de-gridder, tcgen05 Gram, fused SARA, 16 CTAs per SM); 1: read each
+ * cube's choices from the cache file when it holds the cube's key (device name,
+ * compute capability, n1 x n2, L, Qy x Qx, B, total visibilities), else measure them in
+ * fhs_create (pattern inputs, CUDA events: one warm-up, three timed launches per
+ * candidate) and write them to the file; 2: always measure, then write.  cache_path:
+ * a JSON object of objects of numbers, or NULL for no file.  The file is replaced
+ * atomically (write + rename).  Errors: INVALID_ARG (mode). */
+fhs_status fhs_set_autotune(int32_t mode, const char* cache_path);
+/* The choices of a cube.  Errors: INVALID_ARG. */
+fhs_status fhs_get_tuning(const fhs_ctx* ctx, int32_t cube, fhs_tuning* out);
+
 fhs_status fhs_set_wait_limit(int64_t spins);
 fhs_status fhs_set_alloc_limit(uint64_t bytes);
 

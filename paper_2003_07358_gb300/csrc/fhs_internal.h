@@ -82,6 +82,14 @@ struct Cube {
   // DDE-extended G (Section 2.1): kernel half-width R (-1: plain Kaiser-Bessel rows),
   // kernels [n_kern][2R+1][2R+1], kernel of each visibility (internal order), per kernel
   // sum of |Re| + |Im| (rounded up), per (channel, tile) largest extended-footprint count
+  // launch choices of the autotuner (defaults: tile-staged de-gridder, tensor-core Gram
+  // where L <= 32, fused SARA tiles, 16 CTAs per SM for the l2,1 dual pass)
+  int degrid_tiled = 1;
+  int gram_tc = 1;
+  int sara_fast = 1;
+  int prox_cps = 16;
+  int tuned = 0;                             // 0 defaults, 1 measured, 2 from the cache file
+  double tune_ms[10] = {0};
   int dde_R = -1;
   int dde_nkern = 0;
   float2* d_dde_kern = nullptr;
@@ -174,6 +182,10 @@ void launch_fft_adjoint_fast(fhs_ctx* ctx, const Cube& cb, float2* grid, float* 
                              bool accumulate, cudaStream_t st);
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st);
 void encode_degrid_maps(fhs_ctx* ctx);
+void encode_cube_maps(Cube& cb, const float2* grid);
+void launch_fill_pattern(float* p, int64_t n, uint32_t seed, cudaStream_t st);
+void launch_gram(fhs_ctx* ctx, const Cube& cb, const float* xcheck, const float* P, bool tc, cudaStream_t st);
+int num_sms();   // streaming multiprocessors of the current device
 unsigned read_device_status(bool clear);
 int degrid_tiled_parts(const Cube& cb);
 void launch_degrid_pdfb_tiled(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,

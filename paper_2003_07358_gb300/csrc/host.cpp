@@ -5,10 +5,13 @@
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
 #include <complex>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -22,6 +25,18 @@ std::atomic<uint64_t> g_launches{0};
 }
 
 void fhs::note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+int fhs::num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        v <= 0)
+      return 152;
+    n = v;
+  }
+  return n;
+}
 
 namespace {
 
@@ -289,7 +304,7 @@ void upload(T* dst, const T* src, size_t n, cudaStream_t st) {
   if (n) FHS_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, st));
 }
 
-void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
+void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st, int tile) {
   FHS_REQUIRE(d.M && d.uv && d.eta && d.mu_bar && d.eps, FHS_ERR_INVALID_ARG, "NULL host array in cube descriptor");
   FHS_REQUIRE(pow2(d.n1) && pow2(d.n2) && d.n1 >= 16 && d.n2 >= 16, FHS_ERR_UNSUPPORTED,
               "n1, n2 must be powers of two >= 16");
@@ -393,7 +408,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st) {
     cb.max_M = std::max(cb.max_M, m);
   }
   cb.n_vis = cb.vis_off[d.L];
-  cb.tile = std::min(kGridTile, std::min(cb.K1, cb.K2));
+  cb.tile = std::min(tile, std::min(cb.K1, cb.K2));
   cb.ntile_r = cb.K1 / cb.tile;
   cb.ntile_c = cb.K2 / cb.tile;
   const int T = cb.tile;
@@ -598,7 +613,7 @@ bool use_fast(fhs_ctx* ctx, const Cube& cb) { return ctx->path == FHS_PATH_FAST 
 
 void sara_dual(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* W, const float* theta, float* A) {
   cudaStream_t st = ctx->stream;
-  if (use_fast(ctx, cb)) {
+  if (use_fast(ctx, cb) && cb.sara_fast) {
     ensure_coef(ctx);
     set_ll1_offsets(ctx, cb);
     launch_sara_fast(ctx, cb, xcheck, W, theta, A, nullptr, false, st);
@@ -657,7 +672,7 @@ void pdfb_iteration_cube(fhs_ctx* ctx, int c, const fhs_iterate& a) {
       launch_degrid_pdfb_dde(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
                              (float2*)a.state.u_prev, ctx->s.red, np, st);
       timer_mark(ctx, FHS_TIMER_DEGRID, 2 * c + 1);
-    } else if (use_fast(ctx, cb)) {
+    } else if (use_fast(ctx, cb) && cb.degrid_tiled) {
       np = degrid_tiled_parts(cb);
       timer_mark(ctx, FHS_TIMER_DEGRID, 2 * c);
       launch_degrid_pdfb_tiled(cb, ctx->s.grid, (const float2*)a.y, (const float2*)a.state.v, ctx->s.vis,
@@ -699,7 +714,7 @@ void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
 void reweight_cube(fhs_ctx* ctx, const Cube& cb, const float* x, float* theta, float* theta_bar) {
   cudaStream_t st = ctx->stream;
   ensure_coef(ctx);
-  if (use_fast(ctx, cb)) {
+  if (use_fast(ctx, cb) && cb.sara_fast) {
     launch_sara_fast(ctx, cb, x, nullptr, nullptr, nullptr, theta, true, st);
   } else {
     launch_sara_analysis(ctx, cb, x, ctx->s.coef, st);
@@ -908,6 +923,286 @@ void check_iterates(fhs_ctx* ctx, const fhs_iterate* it) {
                 FHS_ERR_INVALID_ARG, "NULL array in fhs_iterate");
   }
 }
+
+// ================================================================ autotuner
+// Per-shape launch choices (the batching form runs many cubes of different shapes,
+// Section 2.4.1): the gridder tile side (32 or 64 cells; it fixes the visibility order,
+// so it is chosen before the cube is built, from trial cubes over the first two
+// channels), then, once the context's scratch exists, the de-gridder (tile-staged or
+// direct), the facet Gram (tcgen05 or CUDA-core float-float), and the SARA pass (fused
+// tiles with 4, 8 or 16 CTAs per SM for the l2,1 pass, or the per-pass kernels).  Every
+// candidate is a kernel the library also runs untuned; each is timed with CUDA events
+// (one warm-up, three timed launches) on pattern inputs.  Choices are kept in a JSON
+// file keyed by device and shape, read back instead of measuring.
+struct TuneChoice {
+  int grid_tile = kGridTile, degrid_tiled = 1, gram_tc = 1, sara_fast = 1, prox_cps = 16, source = 0;
+  double ms[10] = {0};
+};
+
+std::atomic<int> g_tune_mode{0};
+std::mutex g_tune_mu;
+std::string g_tune_path;
+using TuneFile = std::map<std::string, std::map<std::string, double>>;
+
+std::string tune_key(const fhs_cube_desc& d) {
+  int dev = 0;
+  cudaDeviceProp p;
+  FHS_CUDA(cudaGetDevice(&dev));
+  FHS_CUDA(cudaGetDeviceProperties(&p, dev));
+  int64_t m = 0;
+  for (int k = 0; k < d.L * d.B; ++k) m += d.M[k];
+  std::string name = p.name;
+  for (char& ch : name)
+    if (ch == '"' || ch == '\\' || (unsigned char)ch < 32) ch = '_';
+  char buf[320];
+  snprintf(buf, sizeof(buf), "%s|sm_%d%d|n=%dx%d|L=%d|Q=%dx%d|B=%d|M=%lld", name.c_str(), p.major, p.minor, d.n1,
+           d.n2, d.L, d.Qy, d.Qx, d.B, (long long)m);
+  return buf;
+}
+
+// The cache file: one JSON object whose members are objects of numbers.  A missing or
+// unreadable file reads as empty.
+struct JsonScan {
+  const std::string& s;
+  size_t i = 0;
+  void ws() { while (i < s.size() && (s[i] == ' ' || s[i] == '\n' || s[i] == '\r' || s[i] == '\t')) ++i; }
+  bool eat(char c) {
+    ws();
+    if (i < s.size() && s[i] == c) { ++i; return true; }
+    return false;
+  }
+  bool str(std::string& out) {
+    ws();
+    if (i >= s.size() || s[i] != '"') return false;
+    out.clear();
+    for (++i; i < s.size() && s[i] != '"'; ++i) {
+      if (s[i] == '\\' && i + 1 < s.size()) ++i;
+      out.push_back(s[i]);
+    }
+    return i++ < s.size();
+  }
+  bool num(double& v) {
+    ws();
+    const char* b = s.c_str() + i;
+    char* e = nullptr;
+    v = strtod(b, &e);
+    if (e == b) return false;
+    i += (size_t)(e - b);
+    return true;
+  }
+};
+
+TuneFile read_tune_file(const std::string& path) {
+  TuneFile f;
+  FILE* fp = fopen(path.c_str(), "rb");
+  if (!fp) return f;
+  std::string s;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof(buf), fp)) > 0) s.append(buf, n);
+  fclose(fp);
+  JsonScan js{s};
+  TuneFile out;
+  if (!js.eat('{')) return f;
+  if (js.eat('}')) return out;
+  for (;;) {
+    std::string key, name;
+    if (!js.str(key) || !js.eat(':') || !js.eat('{')) return f;
+    std::map<std::string, double>& m = out[key];
+    if (!js.eat('}')) {
+      for (;;) {
+        double v;
+        if (!js.str(name) || !js.eat(':') || !js.num(v)) return f;
+        m[name] = v;
+        if (js.eat('}')) break;
+        if (!js.eat(',')) return f;
+      }
+    }
+    if (js.eat('}')) return out;
+    if (!js.eat(',')) return f;
+  }
+}
+
+void write_tune_file(const std::string& path, const TuneFile& f) {
+  const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+  FILE* fp = fopen(tmp.c_str(), "wb");
+  FHS_REQUIRE(fp, FHS_ERR_INVALID_ARG, "cannot write the tuning cache " + tmp);
+  fprintf(fp, "{\n");
+  size_t k = 0;
+  for (const auto& e : f) {
+    fprintf(fp, "  \"%s\": {", e.first.c_str());
+    size_t j = 0;
+    for (const auto& kv : e.second) fprintf(fp, "%s\"%s\": %.17g", j++ ? ", " : "", kv.first.c_str(), kv.second);
+    fprintf(fp, "}%s\n", ++k < f.size() ? "," : "");
+  }
+  fprintf(fp, "}\n");
+  const bool ok = fclose(fp) == 0;
+  FHS_REQUIRE(ok && rename(tmp.c_str(), path.c_str()) == 0, FHS_ERR_INVALID_ARG,
+              "cannot write the tuning cache " + path);
+}
+
+bool tune_lookup(const std::string& key, TuneChoice& ch) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune_path.empty() || g_tune_mode.load() == 2) return false;
+  TuneFile f = read_tune_file(g_tune_path);
+  auto it = f.find(key);
+  if (it == f.end()) return false;
+  auto get = [&](const char* n, int dflt) {
+    auto v = it->second.find(n);
+    return v == it->second.end() ? dflt : (int)v->second;
+  };
+  ch.grid_tile = get("grid_tile", kGridTile);
+  ch.degrid_tiled = get("degrid_tiled", 1);
+  ch.gram_tc = get("gram_tc", 1);
+  ch.sara_fast = get("sara_fast", 1);
+  ch.prox_cps = get("prox_ctas_per_sm", 16);
+  FHS_REQUIRE((ch.grid_tile == 32 || ch.grid_tile == 64) && ch.prox_cps >= 1 && ch.prox_cps <= 64,
+              FHS_ERR_INVALID_ARG, "tuning cache entry out of range: " + key);
+  for (int k = 0; k < 10; ++k) {
+    auto v = it->second.find("ms_" + std::to_string(k));
+    ch.ms[k] = v == it->second.end() ? 0.0 : v->second;
+  }
+  ch.source = 2;
+  return true;
+}
+
+void tune_store(const std::string& key, const TuneChoice& ch) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune_path.empty()) return;
+  TuneFile f = read_tune_file(g_tune_path);
+  std::map<std::string, double>& m = f[key];
+  m.clear();
+  m["grid_tile"] = ch.grid_tile;
+  m["degrid_tiled"] = ch.degrid_tiled;
+  m["gram_tc"] = ch.gram_tc;
+  m["sara_fast"] = ch.sara_fast;
+  m["prox_ctas_per_sm"] = ch.prox_cps;
+  for (int k = 0; k < 10; ++k) m["ms_" + std::to_string(k)] = ch.ms[k];
+  write_tune_file(g_tune_path, f);
+}
+
+// Mean time of fn over three launches after one warm-up, in ms.
+template <class F>
+double time_ms(cudaStream_t st, F&& fn) {
+  fn();
+  cudaEvent_t a = nullptr, b = nullptr;
+  FHS_CUDA(cudaEventCreate(&a));
+  FHS_CUDA(cudaEventCreate(&b));
+  float ms = 0.f;
+  cudaError_t e = cudaEventRecord(a, st);
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r) fn();
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  FHS_CUDA(e);
+  check_launch("autotune");
+  return ms / 3.0;
+}
+
+// Gridding + tile-staged de-gridding of a trial cube over the first two channels of d
+// with tile side T.
+double trial_tile_ms(const fhs_cube_desc& d, int T, cudaStream_t st) {
+  fhs_cube_desc t = d;
+  t.L = std::min(d.L, 2);
+  Cube cb;
+  float2 *grid = nullptr, *vals = nullptr, *out = nullptr;
+  auto release = [&] {
+    for (void* p : {(void*)grid, (void*)vals, (void*)out})
+      if (p) cudaFree(p);
+    free_cube(cb);
+  };
+  try {
+    build_cube(cb, t, st, T);
+    const size_t ng = (size_t)cb.L * cb.K1 * cb.K2;
+    grid = dalloc<float2>(ng);
+    vals = dalloc<float2>(cb.n_vis);
+    out = dalloc<float2>(cb.n_vis);
+    launch_fill_pattern((float*)vals, 2 * cb.n_vis, 3, st);
+    launch_fill_pattern((float*)grid, 2 * (int64_t)ng, 4, st);
+    encode_cube_maps(cb, grid);
+    const double ms = time_ms(st, [&] {
+      launch_grid(cb, vals, nullptr, nullptr, grid, st);
+      launch_degrid(cb, grid, out, true, st);
+    });
+    FHS_CUDA(cudaStreamSynchronize(st));
+    release();
+    return ms;
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    release();
+    throw;
+  }
+}
+
+// Grid tile of cube d (cache, else trial cubes); the other fields of ch are set from the
+// cache or left for tune_runtime.
+TuneChoice tune_before_build(const fhs_cube_desc& d, cudaStream_t st) {
+  TuneChoice ch;
+  if (tune_lookup(tune_key(d), ch)) return ch;
+  const int kmin = std::min(2 * d.n1, 2 * d.n2);
+  ch.source = 1;
+  if (kmin > 32) {
+    ch.ms[0] = trial_tile_ms(d, 32, st);
+    ch.ms[1] = trial_tile_ms(d, 64, st);
+    ch.grid_tile = ch.ms[0] < ch.ms[1] ? 32 : 64;
+  } else {
+    ch.grid_tile = 32;
+  }
+  return ch;
+}
+
+// Runtime choices of cube c on the context's scratch (pattern inputs), then the cache.
+void tune_after_build(fhs_ctx* ctx, int c, TuneChoice& ch, const std::string& key) {
+  Cube& cb = ctx->cubes[c];
+  if (ch.source == 1) {
+    cudaStream_t st = ctx->stream;
+    const int64_t npix = (int64_t)cb.L * cb.n1 * cb.n2;
+    launch_fill_pattern(ctx->s.img, npix, 5, st);
+    launch_fill_pattern((float*)ctx->s.grid, 2 * (int64_t)cb.L * cb.K1 * cb.K2, 6, st);
+    ch.ms[2] = time_ms(st, [&] { launch_degrid(cb, ctx->s.grid, ctx->s.vis, true, st); });
+    ch.ms[3] = time_ms(st, [&] { launch_degrid(cb, ctx->s.grid, ctx->s.vis, false, st); });
+    ch.degrid_tiled = ch.ms[2] <= ch.ms[3] ? 1 : 0;
+    if (cb.L <= 32) {
+      ch.ms[4] = time_ms(st, [&] { launch_gram(ctx, cb, ctx->s.img, nullptr, true, st); });
+      ch.ms[5] = time_ms(st, [&] { launch_gram(ctx, cb, ctx->s.img, nullptr, false, st); });
+      ch.gram_tc = ch.ms[4] <= ch.ms[5] ? 1 : 0;
+    } else {
+      ch.gram_tc = 0;
+    }
+    ensure_coef(ctx);
+    float* th = dalloc<float>(cb.sara.I);
+    try {
+      ch.ms[6] = time_ms(st, [&] {
+        launch_sara_analysis(ctx, cb, ctx->s.img, ctx->s.coef, st);
+        launch_l21_weights(cb, ctx->s.coef, th, st);
+      });
+      const int cps[3] = {4, 8, 16};
+      int best = 0;
+      for (int k = 0; k < 3; ++k) {
+        cb.prox_cps = cps[k];
+        ch.ms[7 + k] = time_ms(st, [&] { launch_sara_fast(ctx, cb, ctx->s.img, nullptr, nullptr, nullptr, th, true, st); });
+        if (ch.ms[7 + k] < ch.ms[7 + best]) best = k;
+      }
+      ch.prox_cps = cps[best];
+      ch.sara_fast = ch.ms[7 + best] <= ch.ms[6] ? 1 : 0;
+      FHS_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+      cudaStreamSynchronize(st);
+      cudaFree(th);
+      throw;
+    }
+    cudaFree(th);
+    tune_store(key, ch);
+  }
+  cb.tuned = ch.source;
+  cb.degrid_tiled = ch.degrid_tiled;
+  cb.gram_tc = ch.gram_tc;
+  cb.sara_fast = ch.sara_fast;
+  cb.prox_cps = ch.prox_cps;
+  for (int k = 0; k < 10; ++k) cb.tune_ms[k] = ch.ms[k];
+}
 }  // namespace
 
 // ====================================================================== C ABI
@@ -934,7 +1229,17 @@ fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, 
     }
     FHS_CUDA(upload_filters(filt));
     ctx->cubes.resize(ncubes);
-    for (int c = 0; c < ncubes; ++c) build_cube(ctx->cubes[c], cubes[c], ctx->stream);
+    const bool tune = g_tune_mode.load() != 0;
+    std::vector<TuneChoice> choice(ncubes);
+    std::vector<std::string> keys(ncubes);
+    for (int c = 0; c < ncubes; ++c) {
+      // the gridder tile fixes the visibility order: chosen (autotuner) before the build
+      if (tune) {
+        keys[c] = tune_key(cubes[c]);
+        choice[c] = tune_before_build(cubes[c], ctx->stream);
+      }
+      build_cube(ctx->cubes[c], cubes[c], ctx->stream, choice[c].grid_tile);
+    }
     int kmax = 0;
     for (const Cube& cb : ctx->cubes) kmax = std::max(kmax, std::max(cb.K1, cb.K2));
     ctx->Kmax = kmax;
@@ -953,6 +1258,8 @@ fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, 
     FHS_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
     FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    if (tune)
+      for (int c = 0; c < ncubes; ++c) tune_after_build(ctx, c, choice[c], keys[c]);
     FHS_CUDA(cudaStreamSynchronize(ctx->stream));
   } catch (const Fail& e) {
     g_create_err = e.msg;
@@ -1508,6 +1815,29 @@ fhs_status fhs_set_wait_limit(int64_t spins) {
 fhs_status fhs_set_alloc_limit(uint64_t bytes) {
   g_alloc_limit.store(bytes);
   return FHS_OK;
+}
+
+fhs_status fhs_set_autotune(int32_t mode, const char* cache_path) {
+  if (mode < 0 || mode > 2) return FHS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_mode.store(mode);
+  g_tune_path = cache_path ? cache_path : "";
+  return FHS_OK;
+}
+
+fhs_status fhs_get_tuning(const fhs_ctx* cctx, int32_t cube, fhs_tuning* out) {
+  fhs_ctx* ctx = const_cast<fhs_ctx*>(cctx);
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(out, FHS_ERR_INVALID_ARG, "out is NULL");
+    const Cube& cb = get_cube(ctx, cube);
+    out->grid_tile = cb.tile;
+    out->degrid_tiled = cb.degrid_tiled;
+    out->gram_tc = cb.gram_tc;
+    out->sara_fast = cb.sara_fast;
+    out->prox_ctas_per_sm = cb.prox_cps;
+    out->source = cb.tuned;
+    for (int k = 0; k < 10; ++k) out->ms[k] = cb.tune_ms[k];
+  });
 }
 
 fhs_status fhs_set_kernel_timer(fhs_ctx* ctx, int32_t kernel) {

@@ -486,21 +486,32 @@ void launch_nuclear(fhs_ctx* ctx, const Cube& cb, const float* xcheck, float* P,
   if (!weights_mode) launch_nuclear_apply(ctx, cb, xcheck, P, A, st);
 }
 
+// Per-chunk partial Grams of Z_q = D_q S~_q xcheck (+ P_q) into ctx->s.gram: the tcgen05
+// kernel when tc and L <= 32, else the CUDA-core float-float kernel.
+void launch_gram(fhs_ctx* ctx, const Cube& cb, const float* xcheck, const float* P, bool tc, cudaStream_t st) {
+  const int L = cb.L;
+  const int nch = nchunk_max(cb);
+  dim3 gg(nch, cb.Qy * cb.Qx);
+  const int use_P = P != nullptr ? 1 : 0;
+  if (tc && launch_gram_tc(cb, xcheck, P, ctx->s.gram, nch, st)) return;   // counts its launch
+  if (L <= 4) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  else if (L <= 16) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  else k_gram<4><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
+  note_launches(1);
+}
+
 void launch_nuclear_gram_eig(fhs_ctx* ctx, const Cube& cb, const float* xcheck, const float* P,
                              const float* theta_bar, bool weights_mode, float* theta_bar_out, cudaStream_t st) {
   const int L = cb.L;
   const int Q = cb.Qy * cb.Qx;
   const int nch = nchunk_max(cb);
   dim3 gg(nch, Q);
-  int use_P = (P != nullptr && !weights_mode) ? 1 : 0;
-  if (weights_mode)
+  if (weights_mode) {
     k_gram_f64<<<gg, 256, 0, st>>>(xcheck, cb.d_facets, cb.d_win64, cb.n1, cb.n2, L, ctx->s.gram, nch);
-  else if (ctx->path == FHS_PATH_FAST && launch_gram_tc(cb, xcheck, use_P ? P : nullptr, ctx->s.gram, nch, st))
-    ;   // tensor-core Gram (L <= 32)
-  else if (L <= 4) k_gram<1><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
-  else if (L <= 16) k_gram<2><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
-  else k_gram<4><<<gg, 256, 0, st>>>(xcheck, P, cb.d_facets, cb.d_win, cb.n1, cb.n2, L, use_P, ctx->s.gram, nch);
-  if (weights_mode || ctx->path != FHS_PATH_FAST || L > 32) note_launches(1);
+    note_launches(1);
+  } else {
+    launch_gram(ctx, cb, xcheck, P, ctx->path == FHS_PATH_FAST && cb.gram_tc, st);
+  }
   size_t sm = (size_t)2 * L * (L + 1) * sizeof(double) + L * sizeof(double) + 2 * (L / 2 + 1) * sizeof(double) +
               (L + 2 * (L / 2 + 1)) * sizeof(int);
   static bool attr = false;

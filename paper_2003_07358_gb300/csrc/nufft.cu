@@ -1076,6 +1076,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 void encode_degrid_maps(fhs_ctx* ctx) {
+  for (Cube& cb : ctx->cubes) encode_cube_maps(cb, ctx->s.grid);
+}
+
+// TMA maps of cube cb's tile staging over the grid buffer `grid` ([L][K1][K2] float2).
+void encode_cube_maps(Cube& cb, const float2* grid) {
   static EncodeTiledFn encode = nullptr;
   static bool looked = false;
   if (!looked) {
@@ -1086,26 +1091,45 @@ void encode_degrid_maps(fhs_ctx* ctx) {
             cudaSuccess && q == cudaDriverEntryPointSuccess)
       encode = (EncodeTiledFn)fn;
   }
-  for (Cube& cb : ctx->cubes) {
+  {
     cb.tma = false;
     const int T = cb.tile, S = degrid_stage_stride(T);
     // the tile rows must lie in one t-slice of the view and the box must fit the grid
     const bool geom = (cb.N2c == 1 || cb.N1c == T) && T + kTaps - 1 <= 256 && S <= 256 && S <= cb.K2 &&
-                      ((uintptr_t)ctx->s.grid % 16) == 0;
-    if (!encode || !geom) continue;
+                      ((uintptr_t)grid % 16) == 0;
+    if (!encode || !geom) return;
     cuuint64_t dims[4] = {(cuuint64_t)cb.K2, (cuuint64_t)cb.N2c, (cuuint64_t)cb.N1c, (cuuint64_t)cb.L};
     cuuint64_t strides[3] = {(cuuint64_t)cb.K2 * 8, (cuuint64_t)cb.N2c * cb.K2 * 8, (cuuint64_t)cb.K1 * cb.K2 * 8};
     cuuint32_t box_rows[4] = {(cuuint32_t)S, 1, (cuuint32_t)T, 1};
     cuuint32_t box_halo[4] = {(cuuint32_t)S, 1, (cuuint32_t)(kTaps - 1), 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r1 = encode(&cb.tm_rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)ctx->s.grid, dims, strides,
+    CUresult r1 = encode(&cb.tm_rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)grid, dims, strides,
                          box_rows, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    CUresult r2 = encode(&cb.tm_halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)ctx->s.grid, dims, strides,
+    CUresult r2 = encode(&cb.tm_halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)grid, dims, strides,
                          box_halo, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     cb.tma = (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS);
   }
+}
+
+// Deterministic pseudo-random values in [-1, 1) (an integer hash of the index), for the
+// autotuner's trial inputs.
+__global__ void k_fill_pattern(float* __restrict__ p, int64_t n, uint32_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    p[i] = (float)(h >> 8) * (1.f / 8388608.f) - 1.f;
+  }
+}
+
+void launch_fill_pattern(float* p, int64_t n, uint32_t seed, cudaStream_t st) {
+  if (n <= 0) return;
+  const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  k_fill_pattern<<<g, 256, 0, st>>>(p, n, seed);
+  note_launches(1);
 }
 
 cudaError_t set_wait_first(long long spins) {
@@ -1248,7 +1272,7 @@ void launch_vis_scatter(const int64_t* perm, int64_t n, const float2* in, float2
 
 void launch_measure(fhs_ctx* ctx, const Cube& cb, const float* x, float2* y, cudaStream_t st) {
   launch_fft_forward(ctx, cb, x, ctx->s.grid, st);
-  launch_degrid(cb, ctx->s.grid, y, ctx->path == FHS_PATH_FAST, st);
+  launch_degrid(cb, ctx->s.grid, y, ctx->path == FHS_PATH_FAST && cb.degrid_tiled, st);
 }
 
 // host-side replica of kb_weights' first-tap rule (exact same float operations)

@@ -502,7 +502,7 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
   }
   {
     const int64_t N = (int64_t)cb.n1 * cb.n2;
-    const unsigned g = (unsigned)std::min<int64_t>((S.I + 255) / 256, 152 * 16);
+    const unsigned g = (unsigned)std::min<int64_t>((S.I + 255) / 256, (int64_t)num_sms() * cb.prox_cps);
     const float as = (float)(cb.mu / cb.kappa), mu = (float)cb.mu;
     const int wm = weights ? 1 : 0;
     const size_t smem = (size_t)L * 256 * sizeof(float);

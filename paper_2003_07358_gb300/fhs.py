@@ -28,7 +28,7 @@ SYMBOLS = [
     "fhs_proj_l2ball_noalloc", "fhs_noalloc_last_error", "fhs_set_path", "fhs_set_kernel_timer",
     "fhs_kernel_timer_read", "fhs_solve", "fhs_heuristic_params", "fhs_set_preconditioning",
     "fhs_pdfb_iter_host", "fhs_set_wait_limit", "fhs_set_alloc_limit",
-    "fhs_checkpoint_save", "fhs_checkpoint_load", "fhs_set_dde",
+    "fhs_checkpoint_save", "fhs_checkpoint_load", "fhs_set_dde", "fhs_set_autotune", "fhs_get_tuning",
 ]
 MAX_SOLVE_CYCLES = 32
 FHS_PATH = {"fast": 0, "plain": 1}
@@ -79,6 +79,12 @@ class fhs_solve_report(C.Structure):
                 ("res_norm", C.c_double), ("xi_reweight", C.c_double), ("nonfinite", C.c_int32)]
 
 
+class fhs_tuning(C.Structure):
+    _fields_ = [("grid_tile", C.c_int32), ("degrid_tiled", C.c_int32), ("gram_tc", C.c_int32),
+                ("sara_fast", C.c_int32), ("prox_ctas_per_sm", C.c_int32), ("source", C.c_int32),
+                ("ms", C.c_double * 10)]
+
+
 _lib = None
 
 
@@ -125,6 +131,8 @@ def load(path: str = LIB_PATH):
         "fhs_checkpoint_load": ([vp, C.POINTER(fhs_iterate), C.c_char_p], i32),
         "fhs_set_alloc_limit": ([C.c_uint64], i32),
         "fhs_set_dde": ([vp, i32, i32, i32, C.POINTER(C.c_float), C.POINTER(C.c_int32)], i32),
+        "fhs_set_autotune": ([i32, C.c_char_p], i32),
+        "fhs_get_tuning": ([vp, i32, C.POINTER(fhs_tuning)], i32),
         "fhs_pdfb_iter_host": ([vp, C.POINTER(fhs_iterate), C.POINTER(vp), C.POINTER(vp), i32,
                                 C.POINTER(fhs_iter_stats)], i32),
     }
@@ -156,6 +164,14 @@ def fhs_set_alloc_limit(nbytes: int) -> None:
     rc = load().fhs_set_alloc_limit(nbytes)
     if rc != 0:
         raise FhsError(rc, "fhs_set_alloc_limit")
+
+
+def fhs_set_autotune(mode: int, cache_path: str | None = None) -> None:
+    """Autotuning of the contexts created afterwards: 0 defaults, 1 cache then measure,
+    2 always measure; cache_path a JSON file (or None)."""
+    rc = load().fhs_set_autotune(mode, cache_path.encode() if cache_path else None)
+    if rc != 0:
+        raise FhsError(rc, "fhs_set_autotune")
 
 
 def _host_ptr(a, dtype) -> int:
@@ -401,6 +417,13 @@ class Context:
         if u.size != self.sizes(cube)["n_vis"]:
             raise ValueError("U must have one entry per visibility of the cube")
         self._check(self.lib.fhs_set_preconditioning(self.h, cube, n_sub, u.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def fhs_get_tuning(self, cube) -> dict:
+        t = fhs_tuning()
+        self._check(self.lib.fhs_get_tuning(self.h, cube, C.byref(t)))
+        return {"grid_tile": t.grid_tile, "degrid_tiled": t.degrid_tiled, "gram_tc": t.gram_tc,
+                "sara_fast": t.sara_fast, "prox_ctas_per_sm": t.prox_ctas_per_sm,
+                "source": {0: "defaults", 1: "measured", 2: "cache"}[t.source], "ms": list(t.ms)}
 
     def fhs_set_dde(self, cube, kern=None, kidx=None):
         """DDE-extended de-gridding kernels: kern [n_kern][S_d][S_d] complex (first index
