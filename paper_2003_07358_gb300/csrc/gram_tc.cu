@@ -89,6 +89,48 @@ __device__ __forceinline__ void tc_slices(float z, float scale, unsigned short* 
   }
 }
 
+// Paired FP32 arithmetic (add / sub / mul .rn.f32x2 of sm_100-family parts): the same
+// IEEE round-to-nearest operation on both halves, two values per instruction.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+// tc_slices of two values at once: s[k] holds slice k of z0 (low 16 bits) and of z1
+// (high 16 bits) as bf16 bit patterns, the pair order of the operand rows.
+__device__ __forceinline__ void tc_slices2(float z0, float z1, float scale, uint32_t* s) {
+  const uint64_t c128 = f2_pack(128.f, 128.f), magic = f2_pack(12582912.f, 12582912.f);
+  uint64_t r = f2_mul(f2_pack(z0, z1), f2_pack(scale, scale));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t t = f2_mul(r, c128);                       // exact
+    const uint64_t i = f2_sub(f2_add(t, magic), magic);       // rint(t), |t| <= 64
+    r = f2_sub(t, i);                                         // exact
+    float i0, i1;
+    f2_unpack(i, i0, i1);
+    s[k] = __byte_perm(__float_as_uint(i0), __float_as_uint(i1), 0x7632);
+  }
+}
+
 // Value of facet pixel (rr, cc) (linear index p < Nq), channel l: D_q Xcheck + P_q.
 __device__ __forceinline__ float tc_z(const float* __restrict__ xc, const float* __restrict__ P, const NucFacet& f,
                                       float d, size_t xo, size_t N, int Nq, int use_P, int p, int l) {
@@ -102,7 +144,7 @@ __device__ __forceinline__ float tc_z(const float* __restrict__ xc, const float*
 // (from L2) and cuts the operand stages, double-buffered against the MMAs.  Shared
 // memory: two operand stages (32 KB), reused by the epilogue's reduction.
 template <int LP>
-__global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict__ xc, const float* __restrict__ P,
+__global__ void __launch_bounds__(kTcThreads, 2) k_gram_tc(const float* __restrict__ xc, const float* __restrict__ P,
                                                         const NucFacet* __restrict__ facets,
                                                         const float* __restrict__ win, int n1, int n2, int L,
                                                         int use_P, double* __restrict__ part, int nchunk_max) {
@@ -111,11 +153,16 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
   constexpr int RH = 4 * LP;                   // operand rows per half-chunk (64 or 128)
   constexpr int NSTAGE = HP / kTcStageK;       // operand stages per chunk (8 or 16)
   constexpr int NTASK = NH * LP * (kTcStageK / 8);   // (half, channel, 8 pixels) tasks per stage
+  // LP = 16: the chunk's values are loaded once (coalesced) into a shared stash, then
+  // reduced and sliced from there; LP = 32: read twice from global memory (the second
+  // pass hits L2), which keeps the shared memory at two operand stages
+  constexpr bool STASH = LP == 16;
   static_assert(NTASK == kTcThreads, "one slicing task per thread and stage");
   static_assert((size_t)NH * 4 * LP * LP * sizeof(double) <= 2 * (size_t)kTcStageBytes,
                 "the epilogue reduction reuses the operand buffers");
   extern __shared__ __align__(128) unsigned char tc_smem[];
   unsigned char* opnd = tc_smem;                                                 // 2 stages
+  float* zs = reinterpret_cast<float*>(tc_smem + 2 * kTcStageBytes);             // STASH: [LP][kTcChunk]
   double* red = reinterpret_cast<double*>(tc_smem);                              // [NH][4][LP][LP]
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ __align__(8) uint64_t mbar_drain;  // completes when every MMA issued so far has
@@ -123,6 +170,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
   __shared__ int s_max[NH][LP];                // per (half-chunk, channel) max |z| (float bits)
   __shared__ float s_scale[NH][LP];
   __shared__ double s_pow[NH][LP];             // 2^(e + 1)
+  __shared__ __align__(16) int2 s_px[kTcChunk];  // per chunk pixel: window weight d (bits), image offset
 
   const int q = blockIdx.y, chunk = blockIdx.x;
   const NucFacet f = facets[q];
@@ -147,6 +195,39 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
   for (int i = tid; i < NH * LP; i += kTcThreads) (&s_max[0][0])[i] = 0;
   __syncthreads();
 
+  if constexpr (STASH) {
+    // ---- pass 1: thread = pixel, all channels (coalesced along the facet row) into
+    // the stash; then thread (half, channel, 8-pixel segment) takes the maximum of the
+    // 64 values it slices later, 8 lanes per (half, channel)
+#pragma unroll
+    for (int j = 0; j < kTcChunk / kTcThreads; ++j) {
+      const int qq = tid + j * kTcThreads, p = p0 + qq;
+      if (p < Nq) {
+        const int rr = p / w, cc = p - rr * w;
+        const float d = win[f.wy_off + rr] * win[f.wx_off + cc];
+        const size_t xo = (size_t)(f.r0 + rr) * n2 + (f.c0 + cc);
+#pragma unroll
+        for (int l = 0; l < LP; ++l) zs[l * kTcChunk + qq] = l < L ? tc_z(xc, P, f, d, xo, N, Nq, use_P, p, l) : 0.f;
+      } else {
+#pragma unroll
+        for (int l = 0; l < LP; ++l) zs[l * kTcChunk + qq] = 0.f;
+      }
+    }
+    __syncthreads();
+    const int sg = tid % (kTcStageK / 8), shl = tid / (kTcStageK / 8);
+    const int stl = shl % LP, sth = shl / LP;
+    float m = 0.f;
+#pragma unroll
+    for (int st2 = 0; st2 < NSTAGE; ++st2) {
+      const float4* z4 = reinterpret_cast<const float4*>(zs + stl * kTcChunk + sth * HP + st2 * kTcStageK + sg * 8);
+      const float4 a = z4[0], b = z4[1];
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w))));
+    }
+#pragma unroll
+    for (int o = 1; o < kTcStageK / 8; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (sg == 0) s_max[sth][stl] = __float_as_int(m);
+  } else {
   // ---- pass 1: thread = pixel (one division, one window weight), all channels
   // (coalesced along the facet row); maxima in registers, warp shuffles, one shared
   // atomic per warp and (half, channel)
@@ -161,14 +242,17 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
       constexpr int JH = HP / kTcThreads;              // iterations per half-chunk
       const int h = j / JH;                            // compile-time after unrolling
       const int p = p0 + tid + j * kTcThreads;
+      int2 px = make_int2(0, 0);
       if (p < Nq) {
         const int rr = p / w, cc = p - rr * w;
         const float d = win[f.wy_off + rr] * win[f.wx_off + cc];
-        const size_t xo = (size_t)(f.r0 + rr) * n2 + (f.c0 + cc);
+        const int xo = (f.r0 + rr) * n2 + (f.c0 + cc);     // < 2^24 (n1, n2 <= 4096)
+        px = make_int2(__float_as_int(d), xo);
 #pragma unroll
         for (int l = 0; l < LP; ++l)
-          if (l < L) mx[h][l] = fmaxf(mx[h][l], fabsf(tc_z(xc, P, f, d, xo, N, Nq, use_P, p, l)));
+          if (l < L) mx[h][l] = fmaxf(mx[h][l], fabsf(tc_z(xc, P, f, d, (size_t)xo, N, Nq, use_P, p, l)));
       }
+      s_px[tid + j * kTcThreads] = px;
     }
 #pragma unroll
     for (int h = 0; h < NH; ++h)
@@ -179,6 +263,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0 && l < L) atomicMax(&s_max[h][l], __float_as_int(m));
       }
+  }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
@@ -202,20 +287,33 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
   const float sc = s_scale[th][tl];
   bool ok = true;
   unsigned phase[2] = {0u, 0u};
-  // the 8 values of a stage; stage s + 1's loads are issued before stage s is sliced
+  // the 8 values of a stage (window weights and offsets from the pixel table); stage
+  // s + 1's loads are issued before stage s is sliced
+  const float* xcl = xc + (size_t)(chan ? tl : 0) * N;
+  const float* Pl = use_P ? P + f.p_off + (size_t)(chan ? tl : 0) * Nq : P;
   auto load8 = [&](int s, float* zv) {
-    int p = p0 + th * HP + s * kTcStageK + k0;
-    int rr = p / w, cc = p - rr * w;
+    const int q0 = th * HP + s * kTcStageK + k0;       // chunk-local pixel
+    if constexpr (STASH) {
+      const float4* z4 = reinterpret_cast<const float4*>(zs + tl * kTcChunk + q0);
+      const float4 a = z4[0], b = z4[1];
+      zv[0] = a.x; zv[1] = a.y; zv[2] = a.z; zv[3] = a.w;
+      zv[4] = b.x; zv[5] = b.y; zv[6] = b.z; zv[7] = b.w;
+      return;
+    }
+    const int4* t4 = reinterpret_cast<const int4*>(s_px + q0);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      float v = 0.f;
-      if (chan && p < Nq) {
-        const float d = win[f.wy_off + rr] * win[f.wx_off + cc];
-        v = tc_z(xc, P, f, d, (size_t)(f.r0 + rr) * n2 + (f.c0 + cc), N, Nq, use_P, p, tl);
+    for (int jj = 0; jj < 4; ++jj) {
+      const int4 e = t4[jj];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int p = p0 + q0 + 2 * jj + u;
+        float v = 0.f;
+        if (chan && p < Nq) {
+          v = __int_as_float(u ? e.z : e.x) * xcl[u ? e.w : e.y];
+          if (use_P) v += Pl[p];
+        }
+        zv[2 * jj + u] = v;
       }
-      zv[j] = v;
-      ++p;
-      if (++cc == w) { cc = 0; ++rr; }
     }
   };
   float zn[8];
@@ -232,19 +330,14 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
       phase[buf] ^= 1u;
     }
     if (__syncthreads_or(!ok)) { ok = false; break; }
-    unsigned short sl[8][4];
+    uint32_t sl[4][4];                          // [pixel pair][slice]
 #pragma unroll
-    for (int j = 0; j < 8; ++j) tc_slices(zv[j], sc, sl[j]);
+    for (int j = 0; j < 4; ++j) tc_slices2(zv[2 * j], zv[2 * j + 1], sc, sl[j]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int row = th * RH + k * LP + tl;
       const int off = (k0 / 16) * 4096 + ((k0 / 8) & 1) * 128 + (row / 8) * 256 + (row % 8) * 16;
-      uint4 v;
-      v.x = (unsigned)sl[0][k] | ((unsigned)sl[1][k] << 16);
-      v.y = (unsigned)sl[2][k] | ((unsigned)sl[3][k] << 16);
-      v.z = (unsigned)sl[4][k] | ((unsigned)sl[5][k] << 16);
-      v.w = (unsigned)sl[6][k] | ((unsigned)sl[7][k] << 16);
-      *reinterpret_cast<uint4*>(ob + off) = v;
+      *reinterpret_cast<uint4*>(ob + off) = make_uint4(sl[0][k], sl[1][k], sl[2][k], sl[3][k]);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -353,7 +446,9 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(const float* __restrict_
   }
 }
 
-static size_t gram_tc_smem(int) { return 2 * (size_t)kTcStageBytes; }
+static size_t gram_tc_smem(int LP) {
+  return 2 * (size_t)kTcStageBytes + (LP == 16 ? (size_t)LP * kTcChunk * sizeof(float) : 0);
+}
 
 bool launch_gram_tc(const Cube& cb, const float* xcheck, const float* P, double* part, int nchunk_max,
                     cudaStream_t st) {
