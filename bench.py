@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-snr-gap", action="store_true")
     ap.add_argument("--no-dde", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--lanes", type=int, default=1, choices=[1, 2, 3, 4],
+                    help="fhs_set_lanes: sub-cubes of an iteration on 1 to 4 concurrent lanes")
+    ap.add_argument("--autotune", type=int, default=0, choices=[0, 1, 2],
+                    help="fhs_set_autotune mode for the contexts of the bench (0 defaults, 1 cache then measure, "
+                         "2 measure); the choices are reported per shape")
     ap.add_argument("--dry-run", action="store_true",
                     help="set up the ranks (gloo, CPU) and print each rank's sub-cube seed offset, nothing else")
     return ap.parse_args()
@@ -283,6 +289,98 @@ def dde_measurement(args, torch, log, sm_mhz) -> dict:
     dt = time.perf_counter() - t0
     out["oracle"] = {"vis_per_s_degrid_plus_grid": round(4000 / dt, 1), "cores": 1,
                      "sample": "4000 visibilities of channel 0 on a 2048^2 grid, de-gridding then gridding"}
+    return out
+
+
+# ------------------------------------------------ mixed-size batch (Section 2.4.1)
+def batch_measurement(args, torch, log) -> dict:
+    """The mixed-size batch: 16 independent cubes of uneven shapes (sides 128..768, 3 * 2^m
+    sides included; 8..48 channels; 1..6 facets a side; 0.3..2 visibilities per pixel) in
+    one context, one CUDA graph per iteration over all of them.  Data y = Phi x + noise
+    formed with the library; parameters from the noise levels on the device
+    (fhs_heuristic_params).  Times 1, 2 and 4 lanes (fhs_set_lanes) and reports the
+    iterations per second of the whole batch with the fastest, and the launch choices
+    per shape."""
+    from paper_2003_07358_gb300.fhs import Context, CubeParams
+    specs = fs.batch_specs()
+    cps, skies = [], []
+    for spec in specs:
+        rng = np.random.default_rng(spec.seed)
+        sources = fs.sky_sources(spec, rng)
+        base = fs.base_uv(spec, rng)
+        blocks = fs.radial_blocks(base, spec.B)
+        perm = np.concatenate(blocks)
+        chans = fs.subcube_channels(spec, 0)
+        uv = np.concatenate([fs.channel_uv(base, spec, l)[perm] for l in chans])
+        M_lb = np.array([[b.size for b in blocks]] * spec.L, dtype=np.int64)
+        cps.append(CubeParams(n1=spec.n, n2=spec.n, L=spec.L, Qy=spec.Q, Qx=spec.Q, overlap=spec.overlap,
+                              window=spec.window, M_lb=M_lb, uv=uv, eta=np.ones(spec.L), mu=0.0,
+                              mu_bar=np.zeros(spec.Q * spec.Q), eps=np.zeros((spec.L, spec.B))))
+        skies.append((sources, chans, M_lb))
+    t0 = time.time()
+    ctx = Context(cps)
+    log(f"batch context ({len(specs)} cubes) created in {time.time() - t0:.1f} s")
+    dev = ctx.device
+    gen = torch.Generator(device=dev)
+    its = []
+    for c, spec in enumerate(specs):
+        sources, chans, M_lb = skies[c]
+        x = torch.empty((spec.L, spec.n, spec.n), device=dev)
+        for i, l in enumerate(chans):
+            x[i].copy_(torch.from_numpy(fs.render_channel(spec, sources, int(l)).astype(np.float32)))
+        sz = ctx.sizes(c)
+        y = torch.empty(sz["n_vis"], dtype=torch.complex64, device=dev)
+        ctx.fhs_measure(c, x, y)
+        zero = torch.zeros_like(y)
+        tmp = torch.empty_like(y)
+        dn = ctx.fhs_proj_l2ball_blocks(c, y, zero, tmp).reshape(spec.L, spec.B)
+        Ml = M_lb.sum(axis=1)
+        sigma = np.sqrt((dn ** 2).sum(axis=1)) / np.sqrt(Ml) * 10 ** (-spec.isnr_db / 20)
+        gen.manual_seed(spec.seed)
+        off = 0
+        for i in range(spec.L):
+            m = int(Ml[i])
+            y[off:off + m] += float(sigma[i]) * torch.randn(m, dtype=torch.complex64, device=dev, generator=gen)
+            off += m
+        ctx.fhs_heuristic_params(c, sigma, power_iters=10)
+        X = torch.zeros_like(x)
+        its.append({"X": X, "Xcheck": torch.zeros_like(X), "y": y, "state": ctx.new_state(c)})
+        del x, zero, tmp
+    stream = ctx.stream
+    k = 5
+
+    def timed(lanes):
+        ctx.fhs_set_lanes(lanes)
+        for _ in range(3):
+            ctx.fhs_pdfb_iter(its, 1, want_stats=False)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            ctx.fhs_pdfb_iter(its, 1, want_stats=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    lane_ms = {n: round(timed(n), 3) for n in (1, 2, 4)}
+    best = min(lane_ms, key=lane_ms.get)
+    ms = timed(best)
+    st = ctx.fhs_pdfb_iter(its, 1, want_stats=True)
+    tuning = {}
+    for c, spec in enumerate(specs):
+        t = ctx.fhs_get_tuning(c)
+        tuning[spec.name] = {kk: t[kk] for kk in ("grid_tile", "degrid_tiled", "gram_tc", "sara_fast",
+                                                  "prox_ctas_per_sm", "source")}
+    out = {"workload": "mixed-size batch: 16 cubes, sides 128..768 (3 * 2^m included), L 8..48, 1..6 facets a side, "
+                       "M/N 0.3..2, B 1..4",
+           "cubes": len(specs), "pixel_channels": int(sum(sp.n * sp.n * sp.L for sp in specs)),
+           "visibilities": int(sum(sp.M * sp.L for sp in specs)), "ms_per_iteration": round(ms, 3),
+           "iter_per_s": round(1000.0 / ms, 3), "lanes": ctx.fhs_get_lanes(), "timed_iterations": k,
+           "ms_per_iteration_by_lanes": lane_ms,
+           "xi_last": [round(s_["xi"], 6) for s_ in st], "choices_by_cube": tuning}
+    ctx.close()
+    log(f"batch: {ms:.2f} ms per iteration")
     return out
 
 
@@ -524,7 +622,17 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
+    if args.autotune:
+        from paper_2003_07358_gb300.fhs import fhs_set_autotune
+        fhs_set_autotune(args.autotune, os.path.join(tempfile.gettempdir(), f"fhs_autotune_rank{rank}.json"))
     ctx, its = setup(spec, torch, rank, args.opnorm_iters, log)
+    ctx.fhs_set_lanes(args.lanes)
+    tuning = {}
+    for c in range(spec.C):
+        t = ctx.fhs_get_tuning(c)
+        key = f"{spec.n}x{spec.n} L={spec.Lc} Q={spec.Q}x{spec.Q} B={spec.B} M={spec.M}"
+        tuning.setdefault(key, {k: t[k] for k in ("grid_tile", "degrid_tiled", "gram_tc", "sara_fast",
+                                                  "prox_ctas_per_sm", "source")})
     stream = ctx.stream
 
     def barrier():
@@ -552,6 +660,7 @@ def main():
     e1.record(stream)
     barrier()
     launches = ctx.fhs_kernel_launches() - l0
+    lanes = ctx.fhs_get_lanes()
     clocks = sampler.stop()
     grid_ms, grid_n = ctx.fhs_kernel_timer_read()
     ctx.fhs_set_kernel_timer(None)
@@ -660,6 +769,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_dde:
         dde_line = dde_measurement(args, torch, log, clocks.get("sm_mhz"))
 
+    batch_line = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch_line = batch_measurement(args, torch, log)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = time.time()
@@ -682,11 +795,12 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": spec.name, "n": spec.n, "L": spec.L, "subcubes": spec.C,
                            "facets": f"{spec.Q}x{spec.Q}", "vis_per_channel": spec.M, "blocks": spec.B,
-                           "path": "FP32 fused kernels (FP64 reductions)",
+                           "path": "FP32 fused kernels (FP64 reductions)", "lanes": lanes,
                            "l2": "working set ~100 GB >> 129 MB L2; no flush"},
                 "roofline": roofline, "operators": ops, "cpu_baseline": cpu, "e2e": e2e,
-                "plain_fp32_path": plain, "snr_gap_vs_fp64": gaps, "dde_degridding": dde_line, "clocks": clocks,
-                "gpu_launches": launches}
+                "plain_fp32_path": plain, "snr_gap_vs_fp64": gaps, "dde_degridding": dde_line, "mixed_size_batch": batch_line,
+                "clocks": clocks,
+                "autotune_by_shape": tuning, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "CubeSpec", "WORKLOADS", "workload", "frequencies", "subcube_channels",
     "sky_sources", "render_channel", "sky_cube", "base_uv", "channel_uv", "radial_blocks", "unit_noise",
-    "ProblemInputs", "make_inputs", "DdeInputs", "dde_inputs",
+    "ProblemInputs", "make_inputs", "DdeInputs", "dde_inputs", "BATCH_SIDES", "batch_specs",
 ]
 
 
@@ -104,6 +104,29 @@ WORKLOADS = {
 
 def workload(name: str, **over) -> CubeSpec:
     return replace(WORKLOADS[name], **over)
+
+
+# The mixed-size batch: 16 independent cubes of uneven shapes (Section 2.4.1: sub-cubes
+# are separate problems), image sides 128..768 (including 3 * 2^m sides), 8..48
+# channels, 1..6 facets a side, 0.3..2 visibilities per pixel.
+BATCH_SIDES = (128, 192, 256, 384, 512, 768)
+
+
+def batch_specs(n_cubes: int = 16, seed: int = 3000) -> list[CubeSpec]:
+    """Seeded shapes of the mixed-size batch (draw order: side, channels, facets,
+    visibility ratio, blocks, per cube); cube k has seed `seed + k`.  The largest side
+    appears at least once."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_cubes):
+        n = int(BATCH_SIDES[rng.integers(len(BATCH_SIDES))]) if k else BATCH_SIDES[-1]
+        L = int(rng.integers(8, 49))
+        Q = int(rng.integers(1, 7))
+        mr = float(rng.uniform(0.3, 2.0))
+        B = int(rng.integers(1, 5))
+        out.append(CubeSpec(f"batch cube {k}: {n}x{n}, L={L}, {Q}x{Q} facets, M={mr:.2f}N, B={B}", n=n, L=L, C=1,
+                            Q=Q, overlap=0.1, m_ratio=mr, B=B, isnr_db=40.0, n_blobs=20, seed=seed + k))
+    return out
 
 
 def frequencies(spec: CubeSpec) -> np.ndarray:

@@ -255,6 +255,22 @@ fhs_status fhs_set_params(fhs_ctx* ctx, int32_t cube, double tau, double zeta, d
  * path that the fast one is measured against).  Both compute the same operators. */
 enum { FHS_PATH_FAST = 0, FHS_PATH_PLAIN = 1 };
 fhs_status fhs_set_path(fhs_ctx* ctx, int32_t path);
+/* Concurrent lanes of fhs_pdfb_iter on the fast path (a scheduling choice; the paper's
+ * sub-cubes are independent problems, Section 2.4.1).  With lanes = 2..4 and as many
+ * cubes, the cubes are dealt to the lanes (largest first, each to the lane with the
+ * least work so far, work ~ L n1 n2 + visibilities) and every lane runs its cubes on
+ * its own CUDA streams with its own scratch buffers inside the iteration's graph, so
+ * that the launches of cubes too small to fill the GPU run side by side.  Default 1:
+ * cubes whose launches fill the GPU on their own gain nothing from sharing it.  Each
+ * further lane's scratch (about the size of the first: the largest cube's grids,
+ * wavelet coefficients and visibility buffers) is allocated by the next fhs_pdfb_iter;
+ * lanes that the device memory cannot hold are not made (no error).  Lowering the
+ * count frees the lanes above it.  Results do not depend on the lane count: every
+ * cube's arithmetic is the same, bit for bit.  fhs_get_lanes reports the lanes the next
+ * iteration uses (1 until the further lanes exist).  Errors: INVALID_ARG (lanes not in
+ * [1, 4]). */
+fhs_status fhs_set_lanes(fhs_ctx* ctx, int32_t lanes);
+fhs_status fhs_get_lanes(const fhs_ctx* ctx, int32_t* lanes);
 /* Number of CUDA kernels this library has launched in this process so far. */
 uint64_t fhs_kernel_launches(void);
 

@@ -63,8 +63,8 @@ __device__ __forceinline__ float2 dde_degrid_one(const float2* __restrict__ gl, 
   for (int k = lane; k < SD * SD; k += 32) s.ker[k] = Km[k];
   for (int k = lane; k < F * F; k += 32) {
     const int r = k / F, c = k - r * F;
-    const int row = phys_row2((kr - R + r) & (vg.K1 - 1), vg);
-    s.win[k] = gl[(size_t)row * vg.K2 + ((kc - R + c) & (vg.K2 - 1))];
+    const int row = phys_row2(wrap1(kr - R + r, vg), vg);
+    s.win[k] = gl[(size_t)row * vg.K2 + wrap2(kc - R + c, vg)];
   }
   __syncwarp();
   float wc[kTaps], wr[kTaps];
@@ -162,7 +162,10 @@ __global__ void __launch_bounds__(kDdeThreads) k_degrid_dde(const float2* __rest
 
 // Local start (mod K) of a footprint that starts at absolute cell k, relative to tile
 // start t0: cells (d + r) mod K < T of the footprint lie in the tile.
-__device__ __forceinline__ int dde_local(int k, int t0, int K) { return (k - t0) & (K - 1); }
+__device__ __forceinline__ int dde_local(int k, int t0, int K, int pw) {
+  const int d = k - t0;
+  return pw ? (d & (K - 1)) : ((d % K) + K) % K;
+}
 
 // Whether a footprint of F cells starting at local offset d (mod K) meets [0, T).
 __device__ __forceinline__ bool dde_meets(int d, int F, int T, int K) { return d < T || d + F - 1 >= K; }
@@ -177,7 +180,7 @@ __device__ __forceinline__ void dde_grid_one(int* are, int* aim, int TP, int T, 
   if (MODE == 1) {
     for (int k = lane; k < F * F; k += 32) {
       const int r = k / F, c = k - r * F;
-      const int lr = (dr + r) & (vg.K1 - 1), lc = (dc + c) & (vg.K2 - 1);
+      const int lr = wrap1(dr + r, vg), lc = wrap2(dc + c, vg);
       if (lr < T && lc < T) atomicAdd(are + lr * TP + lc, 1);
     }
     return;
@@ -213,7 +216,7 @@ __device__ __forceinline__ void dde_grid_one(int* are, int* aim, int TP, int T, 
   // column pass and the tile's cells: x[r][c] = sum_b w_c[b] H[r][c - b]
   for (int k = lane; k < F * F; k += 32) {
     const int r = k / F, c = k - r * F;
-    const int lr = (dr + r) & (vg.K1 - 1), lc = (dc + c) & (vg.K2 - 1);
+    const int lr = wrap1(dr + r, vg), lc = wrap2(dc + c, vg);
     if (lr >= T || lc >= T) continue;
     float2 x = make_float2(0.f, 0.f);
 #pragma unroll
@@ -299,8 +302,8 @@ __global__ void __launch_bounds__(kDdeThreads) k_grid_dde(const float2* __restri
         float xr, xc;
         const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
         const int kc = kb_first(w.x, vg.tc.hi_c, vg.tc.lo_c, xc);
-        if (dde_meets(dde_local(kr - R, t0r, vg.K1), F, T, vg.K1) &&
-            dde_meets(dde_local(kc - R, t0c, vg.K2), F, T, vg.K2))
+        if (dde_meets(dde_local(kr - R, t0r, vg.K1, vg.pw), F, T, vg.K1) &&
+            dde_meets(dde_local(kc - R, t0c, vg.K2, vg.pw), F, T, vg.K2))
           m = fmaxf(m, fmaxf(fabsf(val.x), fabsf(val.y)) * kl1[kidx[i]]);
       }
     }
@@ -335,8 +338,8 @@ __global__ void __launch_bounds__(kDdeThreads) k_grid_dde(const float2* __restri
         const float2 w = uv[vbase + k];
         const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
         const int kc = kb_first(w.x, vg.tc.hi_c, vg.tc.lo_c, xc);
-        dr = dde_local(kr - R, t0r, vg.K1);
-        dc = dde_local(kc - R, t0c, vg.K2);
+        dr = dde_local(kr - R, t0r, vg.K1, vg.pw);
+        dc = dde_local(kc - R, t0c, vg.K2, vg.pw);
         hit = dde_meets(dr, F, T, vg.K1) && dde_meets(dc, F, T, vg.K2);
       }
       unsigned mask = __ballot_sync(0xffffffffu, hit);

@@ -272,7 +272,7 @@ static void colA_adj_n(const Cube& cb, const float2* grid, float* out, const flo
 // writes the real and imaginary parts of each output as two image columns.  Bytes per
 // channel and direction: 68N against 100N for the unpacked column-first order.
 bool fft_forward_packed(const Cube& cb) {
-  return cb.K2 >= 2048 && cb.K2 <= 8192 && cb.N1c >= 64 && cb.N1c <= 256 && cb.n2 % 64 == 0 &&
+  return cb.pow2 && cb.K2 >= 2048 && cb.K2 <= 8192 && cb.N1c >= 64 && cb.N1c <= 256 && cb.n2 % 64 == 0 &&
          cb.n2 * 2 == cb.K2;
 }
 

@@ -19,6 +19,7 @@ constexpr int kDdeMaxR = 4;       // DDE kernels up to 9 x 9 (extended footprint
 constexpr int kLevels = 4;        // SARA decomposition levels
 constexpr int kMaxB = 16;         // data blocks per channel
 constexpr int kMaxL = 64;         // channels per cube
+constexpr int kMaxLanes = 4;      // concurrent lanes of an iteration (fhs_set_lanes)
 constexpr int kMaxFilt = 16;      // longest Daubechies filter (db8)
 constexpr int kMaxSolveCycles = FHS_MAX_SOLVE_CYCLES;
 
@@ -43,8 +44,17 @@ struct NucFacet {                    // one nuclear facet
   int wy_off, wx_off;                // offsets of its 1-D windows in the window tables
 };
 
+// Radix plan of a mixed-radix (4, 2, 3) DFT of length n = 2^a 3^b.
+struct GenPlan {
+  int n;
+  int npass;
+  int radix[24];
+};
+
 struct Cube {
   int n1, n2, L, Qy, Qx, B, window;
+  bool pow2 = true;                          // n1, n2 powers of two (else 3 * 2^m: mixed-radix DFTs)
+  GenPlan plan_r{}, plan_c{};                // column (length K1) and row (length K2) plans
   double rho, tau, zeta, kappa, mu;
   std::vector<double> eta, mu_bar, eps;     // host copies
   int K1, K2;
@@ -99,11 +109,13 @@ struct Cube {
   float* d_gamma = nullptr;                  // [L*B] 1 / max U of the block
   float* d_eta = nullptr;                    // [L]
   float* d_mubar = nullptr;                  // [Q]
-  // TMA descriptors of the degridder's tile staging over the context's grid scratch,
-  // viewed as [L][N1c][N2c][K2] (rows in the column transform's digit-reversed order):
-  // the T tile rows and the 6 halo rows of a grid tile
-  CUtensorMap tm_rows, tm_halo;
-  bool tma = false;
+  // TMA descriptors of the degridder's tile staging over a grid scratch buffer, viewed
+  // as [L][N1c][N2c][K2] (rows in the column transform's digit-reversed order): the T
+  // tile rows and the 6 halo rows of a grid tile.  Two slots: the grid of each lane of
+  // concurrent cubes; a launch uses the slot encoded over the grid it is given, and the
+  // asynchronous copies when there is none.
+  CUtensorMap tm_rows[kMaxLanes], tm_halo[kMaxLanes];
+  const float2* tm_grid[kMaxLanes] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 struct Scratch {
@@ -124,10 +136,22 @@ struct Scratch {
   float* nucM = nullptr;     size_t nucM_elems = 0;     // [Q][L][L]
   float* blk_scale = nullptr;                           // [L*B]
   double* blk_out = nullptr;                            // [2][L*B]
-  float* ll1 = nullptr;                                 // synthesised LL1 band of each basis (fused SARA)
+  float* ll1 = nullptr;                                 // LL1 band of each basis (fused SARA)
+  float* ll2 = nullptr;                                 // LL2 band of each basis
+  float* ll3 = nullptr;                                 // LL3 band of each basis
   double* stat = nullptr;                               // per cube: primal partials, then block norms
   size_t stat_stride = 0;
   int64_t ll1_off[8] = {0};                             // per-basis offsets into ll1
+  int64_t ll2_off[8] = {0};                             // into ll2
+  int64_t ll3_off[8] = {0};                             // into ll3
+};
+
+// Streams, events and scratch of one further lane of an iteration.
+struct Lane {
+  Scratch s;
+  cudaStream_t stream = nullptr, aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // this lane's fork to / join from its aux stream
+  cudaEvent_t ev_done = nullptr;                      // the lane's last work (joined by the first lane)
 };
 
 }  // namespace fhs
@@ -148,6 +172,12 @@ struct fhs_ctx {
   // run beside the data term (they read Xcheck and P only) and join before the update of A
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // further lanes of an iteration (fast path, two or more cubes): cube c runs on lane
+  // lane_of[c]; lane k > 0 has its own streams, events and scratch in xl[k - 1]
+  int lanes = 1;                   // requested lanes (fhs_set_lanes)
+  std::vector<fhs::Lane> xl;       // lanes 1.. whose resources exist
+  std::vector<int> lane_of;        // [ncubes] lane of each cube
+  cudaEvent_t ev_lanes_fork = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<const void*> graph_key;
   uint64_t graph_kernels = 0;
@@ -182,7 +212,7 @@ void launch_fft_adjoint_fast(fhs_ctx* ctx, const Cube& cb, float2* grid, float* 
                              bool accumulate, cudaStream_t st);
 void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, cudaStream_t st);
 void encode_degrid_maps(fhs_ctx* ctx);
-void encode_cube_maps(Cube& cb, const float2* grid);
+void encode_cube_maps(Cube& cb, const float2* grid, int slot);
 void launch_fill_pattern(float* p, int64_t n, uint32_t seed, cudaStream_t st);
 void launch_gram(fhs_ctx* ctx, const Cube& cb, const float* xcheck, const float* P, bool tc, cudaStream_t st);
 int num_sms();   // streaming multiprocessors of the current device

@@ -12,6 +12,7 @@
 #include <complex>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -282,6 +283,27 @@ void nuclear_axis(int n, int Q, double rho, int kind, std::vector<int>& start, s
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// n = 2^a 3^b with b >= 1 (the mixed-radix transforms' sizes)
+bool pow2_times3(int n) {
+  if (n <= 0 || n % 3) return false;
+  while (n % 3 == 0) n /= 3;
+  return pow2(n);
+}
+
+// Radix plan of a length-n DFT, n = 2^a 3^b: radix-4 passes, one radix-2 pass when a is
+// odd, then the radix-3 passes.
+GenPlan gen_plan(int n) {
+  GenPlan p{};
+  p.n = n;
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  for (int k = 0; k < a / 2; ++k) p.radix[p.npass++] = 4;
+  if (a % 2) p.radix[p.npass++] = 2;
+  for (int k = 0; k < b; ++k) p.radix[p.npass++] = 3;
+  return p;
+}
+
 // Fault-injection hook: a cap on the device bytes the library allocates on this thread
 // from the start of the last fhs_create (0: none); a request beyond it fails as OOM.
 std::atomic<uint64_t> g_alloc_limit{0};
@@ -306,8 +328,12 @@ void upload(T* dst, const T* src, size_t n, cudaStream_t st) {
 
 void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st, int tile) {
   FHS_REQUIRE(d.M && d.uv && d.eta && d.mu_bar && d.eps, FHS_ERR_INVALID_ARG, "NULL host array in cube descriptor");
-  FHS_REQUIRE(pow2(d.n1) && pow2(d.n2) && d.n1 >= 16 && d.n2 >= 16, FHS_ERR_UNSUPPORTED,
-              "n1, n2 must be powers of two >= 16");
+  const bool p2 = pow2(d.n1) && pow2(d.n2);
+  FHS_REQUIRE(d.n1 >= 16 && d.n2 >= 16 &&
+                  (p2 || ((pow2(d.n1) || pow2_times3(d.n1)) && (pow2(d.n2) || pow2_times3(d.n2)) &&
+                          d.n1 % 16 == 0 && d.n2 % 16 == 0 && d.n1 <= 1536 && d.n2 <= 1536)),
+              FHS_ERR_UNSUPPORTED,
+              "n1, n2 must be powers of two >= 16, or multiples of 16 of the form 2^a 3^b up to 1536");
   FHS_REQUIRE(d.n1 <= 4096 && d.n2 <= 4096, FHS_ERR_UNSUPPORTED, "n1, n2 must be <= 4096");
   FHS_REQUIRE(d.L >= 1 && d.L <= kMaxL, FHS_ERR_UNSUPPORTED, "L must be in [1, 64]");
   FHS_REQUIRE(d.Qy >= 1 && d.Qx >= 1 && d.Qy <= d.n1 / 16 + (d.n1 < 16) && d.Qx <= d.n2 / 16 + (d.n2 < 16),
@@ -328,8 +354,11 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st, int tile) {
   for (double v : cb.eps) FHS_REQUIRE(std::isfinite(v) && v >= 0, FHS_ERR_INVALID_ARG, "eps must be >= 0");
   cb.K1 = 2 * d.n1;
   cb.K2 = 2 * d.n2;
-  if (cb.K1 <= 1024) { cb.N1c = cb.K1; cb.N2c = 1; }
+  cb.pow2 = p2;
+  if (cb.K1 <= 1024 || !p2) { cb.N1c = cb.K1; cb.N2c = 1; }    // one-pass column transform
   else { cb.N1c = 64; cb.N2c = cb.K1 / 64; }
+  cb.plan_r = gen_plan(cb.K1);
+  cb.plan_c = gen_plan(cb.K2);
 
   // SARA layout
   SaraLayout& S = cb.sara;
@@ -409,6 +438,7 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st, int tile) {
   }
   cb.n_vis = cb.vis_off[d.L];
   cb.tile = std::min(tile, std::min(cb.K1, cb.K2));
+  if (cb.K1 % cb.tile || cb.K2 % cb.tile) cb.tile = 32;      // K = 2^a 3^b: a multiple of 32
   cb.ntile_r = cb.K1 / cb.tile;
   cb.ntile_c = cb.K2 / cb.tile;
   const int T = cb.tile;
@@ -435,8 +465,8 @@ void build_cube(Cube& cb, const fhs_cube_desc& d, cudaStream_t st, int tile) {
       float u = d.uv[2 * (off + i)], v = d.uv[2 * (off + i) + 1];
       FHS_REQUIRE(std::isfinite(u) && std::isfinite(v) && fabsf(u) < (float)kPi && fabsf(v) < (float)kPi,
                   FHS_ERR_INVALID_ARG, "uv coordinates must be finite and inside (-pi, pi)");
-      int kr = host_first_tap(v, cb.K1) & (cb.K1 - 1);
-      int kc = host_first_tap(u, cb.K2) & (cb.K2 - 1);
+      int kr = ((host_first_tap(v, cb.K1) % cb.K1) + cb.K1) % cb.K1;
+      int kc = ((host_first_tap(u, cb.K2) % cb.K2) + cb.K2) % cb.K2;
       int tr = kr / T, tc = kc / T, lr = kr % T, lc = kc % T;
       bool down = lr + kTaps - 1 >= T, right = lc + kTaps - 1 >= T;
       int cls = down ? (right ? 2 : 1) : (right ? 3 : 0);
@@ -552,11 +582,17 @@ void alloc_scratch(fhs_ctx* ctx) {
     nm = std::max(nm, (size_t)cb.facets.size() * L * ((L + 3) & ~3));   // M_q^T rows padded to 16 B
     lb = std::max(lb, L * cb.B);
   }
-  size_t ll1 = 0;
+  size_t ll1 = 0, ll2 = 0, ll3 = 0;
   for (const Cube& cb : ctx->cubes) {
-    size_t tot = 0;
-    for (int b = 0; b < 8; ++b) tot += (size_t)cb.L * cb.sara.rows[b][1] * cb.sara.cols[b][1];
-    ll1 = std::max(ll1, tot);
+    size_t t1 = 0, t2 = 0, t3 = 0;
+    for (int b = 0; b < 8; ++b) {
+      t1 += (size_t)cb.L * cb.sara.rows[b][1] * cb.sara.cols[b][1];
+      t2 += (size_t)cb.L * cb.sara.rows[b][2] * cb.sara.cols[b][2];
+      t3 += (size_t)cb.L * cb.sara.rows[b][3] * cb.sara.cols[b][3];
+    }
+    ll1 = std::max(ll1, t1);
+    ll2 = std::max(ll2, t2);
+    ll3 = std::max(ll3, t3);
   }
   s.grid = dalloc<float2>(grid); s.grid_elems = grid;
   size_t pack = 0;
@@ -565,6 +601,8 @@ void alloc_scratch(fhs_ctx* ctx) {
   if (pack) s.pack = dalloc<float2>(pack);
   s.coef_elems = coef;          // allocated on first use of the plain path (ensure_coef)
   s.ll1 = dalloc<float>(ll1);
+  s.ll2 = dalloc<float>(ll2);
+  s.ll3 = dalloc<float>(ll3);
   s.t0 = dalloc<float>(tlx); s.t1 = dalloc<float>(tlx);
   s.t2 = dalloc<float>(tll); s.t3 = dalloc<float>(tll);
   s.t_elems = tlx;
@@ -583,10 +621,161 @@ void alloc_scratch(fhs_ctx* ctx) {
 void free_scratch(Scratch& s) {
   void* ps[] = {s.grid, s.pack, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.img2, s.vis, s.vis2, s.red, s.gram, s.nucM,
                 s.blk_scale,
-                s.blk_out, s.ll1, s.stat};
+                s.blk_out, s.ll1, s.ll2, s.ll3, s.stat};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (s.red_host) cudaFreeHost(s.red_host);
+}
+
+// Further lanes: each has its own streams, events and a scratch set like the first
+// lane's (the plain path's coefficient buffer excepted); all share the statistics
+// region.  Allocated by fhs_pdfb_iter before it captures; lanes that the device memory
+// cannot hold are not made (the context keeps the lanes it has).
+void free_lane(fhs_ctx* ctx, Lane& x, int slot) {
+  if (x.stream) cudaStreamSynchronize(x.stream);
+  if (x.aux) cudaStreamSynchronize(x.aux);
+  Scratch& s = x.s;
+  void* ps[] = {s.grid, s.pack, s.coef, s.t0, s.t1, s.t2, s.t3, s.img, s.vis, s.vis2, s.red, s.gram, s.nucM,
+                s.blk_scale, s.blk_out, s.ll1, s.ll2, s.ll3};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  s = Scratch();
+  if (x.stream) cudaStreamDestroy(x.stream);
+  if (x.aux) cudaStreamDestroy(x.aux);
+  for (cudaEvent_t e : {x.ev_fork, x.ev_join, x.ev_done})
+    if (e) cudaEventDestroy(e);
+  x = Lane();
+  for (Cube& cb : ctx->cubes) cb.tm_grid[slot] = nullptr;
+}
+
+// Frees the lanes from index `keep` on (lane 0 is the context's own).
+void free_lanes(fhs_ctx* ctx, int keep) {
+  while ((int)ctx->xl.size() + 1 > std::max(keep, 1)) {
+    const int k = (int)ctx->xl.size();
+    free_lane(ctx, ctx->xl.back(), k);
+    ctx->xl.pop_back();
+  }
+}
+
+// Makes one more lane like the first; false (nothing kept) when memory is short.
+bool make_lane(fhs_ctx* ctx) {
+  const Scratch& a = ctx->s;
+  Lane x;
+  Scratch& b = x.s;
+  bool ok = true;
+  auto get = [&](auto*& p, size_t n, size_t elem) {
+    using T = std::remove_reference_t<decltype(*p)>;
+    if (!ok || n == 0) return;
+    const uint64_t lim = g_alloc_limit.load();
+    void* q = nullptr;
+    if ((lim && g_alloc_used + n * elem > lim) || cudaMalloc(&q, n * elem) != cudaSuccess) {
+      cudaGetLastError();          // an allocation failure leaves no sticky error
+      ok = false;
+      return;
+    }
+    g_alloc_used += n * elem;
+    p = (T*)q;
+  };
+  size_t ll1 = 0, ll2 = 0, ll3 = 0, tll = 0;
+  for (const Cube& cb : ctx->cubes) {
+    size_t t1 = 0, t2 = 0, t3 = 0;
+    for (int k = 0; k < 8; ++k) {
+      t1 += (size_t)cb.L * cb.sara.rows[k][1] * cb.sara.cols[k][1];
+      t2 += (size_t)cb.L * cb.sara.rows[k][2] * cb.sara.cols[k][2];
+      t3 += (size_t)cb.L * cb.sara.rows[k][3] * cb.sara.cols[k][3];
+      for (int j = 1; j <= kLevels; ++j) tll = std::max(tll, (size_t)cb.L * cb.sara.rows[k][j] * cb.sara.cols[k][j]);
+    }
+    ll1 = std::max(ll1, t1);
+    ll2 = std::max(ll2, t2);
+    ll3 = std::max(ll3, t3);
+  }
+  size_t pack = 0;
+  for (const Cube& cb : ctx->cubes)
+    if (fft_forward_packed(cb)) pack = std::max(pack, (size_t)cb.L * cb.K1 * (cb.n2 / 2));
+  get(b.grid, a.grid_elems, sizeof(float2));
+  get(b.pack, pack, sizeof(float2));
+  get(b.coef, a.coef_elems, sizeof(float));
+  get(b.t0, a.t_elems, sizeof(float));     // separate SARA passes (an autotuner choice)
+  get(b.t1, a.t_elems, sizeof(float));
+  get(b.t2, tll, sizeof(float));
+  get(b.t3, tll, sizeof(float));
+  get(b.img, a.img_elems, sizeof(float));
+  get(b.vis, a.vis_elems, sizeof(float2));
+  if (a.vis2) get(b.vis2, a.vis_elems, sizeof(float2));
+  get(b.red, a.red_elems, sizeof(double));
+  get(b.gram, a.gram_elems, sizeof(double));
+  get(b.nucM, a.nucM_elems, sizeof(float));
+  size_t lb = 0;
+  for (const Cube& cb : ctx->cubes) lb = std::max(lb, (size_t)cb.L * cb.B);
+  get(b.blk_scale, lb, sizeof(float));
+  get(b.blk_out, 2 * lb + 2 * kMaxL, sizeof(double));
+  get(b.ll1, ll1, sizeof(float));
+  get(b.ll2, ll2, sizeof(float));
+  get(b.ll3, ll3, sizeof(float));
+  b.grid_elems = a.grid_elems;
+  b.coef_elems = a.coef_elems;
+  b.img_elems = a.img_elems;
+  b.vis_elems = a.vis_elems;
+  b.red_elems = a.red_elems;
+  b.gram_elems = a.gram_elems;
+  b.nucM_elems = a.nucM_elems;
+  b.t_elems = a.t_elems;
+  b.stat_stride = a.stat_stride;
+  if (ok) {
+    ok = cudaStreamCreateWithFlags(&x.stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&x.aux, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x.ev_join, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x.ev_done, cudaEventDisableTiming) == cudaSuccess;
+  }
+  const int slot = (int)ctx->xl.size() + 1;
+  if (!ok) {
+    free_lane(ctx, x, slot);
+    cudaGetLastError();
+    return false;
+  }
+  b.stat = a.stat;                 // shared: each cube writes its own part
+  for (Cube& cb : ctx->cubes) encode_cube_maps(cb, b.grid, slot);
+  ctx->xl.push_back(x);
+  return true;
+}
+
+// Lanes the next iteration uses: the requested count, at most one per cube, on the fast
+// path (the plain comparison path stays a single stream of direct launches).
+int lanes_in_use(const fhs_ctx* ctx) {
+  if (ctx->path != FHS_PATH_FAST) return 1;
+  return std::max(1, std::min({ctx->lanes, (int)ctx->cubes.size(), (int)ctx->xl.size() + 1}));
+}
+
+// Makes the requested lanes (outside any capture) and deals the cubes to them: largest
+// first, each to the lane with the least work so far (work ~ pixel-channels plus
+// visibilities).
+void ensure_lanes(fhs_ctx* ctx) {
+  const int nc = (int)ctx->cubes.size();
+  if (ctx->path != FHS_PATH_FAST) return;
+  const int want = std::min(ctx->lanes, nc);
+  while ((int)ctx->xl.size() + 1 < want)
+    if (!make_lane(ctx)) {
+      ctx->lanes = (int)ctx->xl.size() + 1;    // not enough device memory for more lanes
+      break;
+    }
+  if (!ctx->ev_lanes_fork && !ctx->xl.empty())
+    FHS_CUDA(cudaEventCreateWithFlags(&ctx->ev_lanes_fork, cudaEventDisableTiming));
+  const int nl = lanes_in_use(ctx);
+  std::vector<int> order(nc);
+  for (int c = 0; c < nc; ++c) order[c] = c;
+  auto work = [&](int c) {
+    const Cube& cb = ctx->cubes[c];
+    return (double)cb.L * cb.n1 * cb.n2 + (double)cb.n_vis;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  std::vector<double> load(nl, 0.0);
+  ctx->lane_of.assign(nc, 0);
+  for (int c : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    ctx->lane_of[c] = k;
+    load[k] += work(c);
+  }
 }
 
 const Cube& get_cube(fhs_ctx* ctx, int32_t c) {
@@ -705,9 +894,45 @@ void pdfb_iteration_cube(fhs_ctx* ctx, int c, const fhs_iterate& a) {
   }
 }
 
-// One iteration of Algorithm 2 on every cube.
+// Exchanges the first lane's streams, events and scratch with lane x's: the launchers
+// use ctx->stream, ctx->aux and ctx->s, so a cube issued between two swaps runs on
+// lane x.  All lanes share the statistics region.
+void swap_lane(fhs_ctx* ctx, Lane& x) {
+  std::swap(ctx->s, x.s);
+  std::swap(ctx->stream, x.stream);
+  std::swap(ctx->aux, x.aux);
+  std::swap(ctx->ev_fork, x.ev_fork);
+  std::swap(ctx->ev_join, x.ev_join);
+}
+
+// One iteration of Algorithm 2 on every cube.  The sub-cubes are independent problems
+// (Section 2.4.1): with several lanes, cube c runs on lane lane_of[c], so that the
+// launches of cubes too small to fill the GPU run side by side.
 void pdfb_iteration(fhs_ctx* ctx, const fhs_iterate* it) {
-  for (int c = 0; c < (int)ctx->cubes.size(); ++c) pdfb_iteration_cube(ctx, c, it[c]);
+  const int nc = (int)ctx->cubes.size();
+  const int nl = lanes_in_use(ctx);
+  if (nl == 1 || (int)ctx->lane_of.size() != nc) {
+    for (int c = 0; c < nc; ++c) pdfb_iteration_cube(ctx, c, it[c]);
+    return;
+  }
+  FHS_CUDA(cudaEventRecord(ctx->ev_lanes_fork, ctx->stream));
+  for (int k = 1; k < nl; ++k) FHS_CUDA(cudaStreamWaitEvent(ctx->xl[k - 1].stream, ctx->ev_lanes_fork, 0));
+  for (int c = 0; c < nc; ++c) {
+    const int k = ctx->lane_of[c] < nl ? ctx->lane_of[c] : 0;
+    if (k > 0) swap_lane(ctx, ctx->xl[k - 1]);
+    try {
+      pdfb_iteration_cube(ctx, c, it[c]);
+    } catch (...) {
+      if (k > 0) swap_lane(ctx, ctx->xl[k - 1]);
+      throw;
+    }
+    if (k > 0) swap_lane(ctx, ctx->xl[k - 1]);
+  }
+  for (int k = 1; k < nl; ++k) {
+    Lane& x = ctx->xl[k - 1];
+    FHS_CUDA(cudaEventRecord(x.ev_done, x.stream));
+    FHS_CUDA(cudaStreamWaitEvent(ctx->stream, x.ev_done, 0));
+  }
 }
 
 // Weights of Algorithm 1 (Eqs. 9-10) of cube c from x, on ctx->stream.
@@ -1121,7 +1346,7 @@ double trial_tile_ms(const fhs_cube_desc& d, int T, cudaStream_t st) {
     out = dalloc<float2>(cb.n_vis);
     launch_fill_pattern((float*)vals, 2 * cb.n_vis, 3, st);
     launch_fill_pattern((float*)grid, 2 * (int64_t)ng, 4, st);
-    encode_cube_maps(cb, grid);
+    encode_cube_maps(cb, grid, 0);
     const double ms = time_ms(st, [&] {
       launch_grid(cb, vals, nullptr, nullptr, grid, st);
       launch_degrid(cb, grid, out, true, st);
@@ -1240,8 +1465,12 @@ fhs_status fhs_create(const fhs_cube_desc* cubes, int32_t ncubes, void* stream, 
       }
       build_cube(ctx->cubes[c], cubes[c], ctx->stream, choice[c].grid_tile);
     }
-    int kmax = 0;
-    for (const Cube& cb : ctx->cubes) kmax = std::max(kmax, std::max(cb.K1, cb.K2));
+    // twiddle table exp(-2 pi i k / Kmax): Kmax is the least common multiple of the grid
+    // sides (2^a 3^b each), so every transform length divides it
+    int kmax = 1;
+    for (const Cube& cb : ctx->cubes)
+      for (int K : {cb.K1, cb.K2}) kmax = std::lcm(kmax, K);
+    FHS_REQUIRE(kmax <= (1 << 16), FHS_ERR_UNSUPPORTED, "grid sides too far apart for one twiddle table");
     ctx->Kmax = kmax;
     std::vector<float2> tw(kmax);
     for (int k = 0; k < kmax; ++k) {
@@ -1291,6 +1520,8 @@ fhs_status fhs_destroy(fhs_ctx* ctx) {
   }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  free_lanes(ctx, 1);
+  if (ctx->ev_lanes_fork) cudaEventDestroy(ctx->ev_lanes_fork);
   for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   for (Cube& cb : ctx->cubes) free_cube(cb);
   free_scratch(ctx->s);
@@ -1617,6 +1848,8 @@ fhs_status fhs_set_preconditioning(fhs_ctx* ctx, int32_t cube, int32_t n_sub, co
     if (!cb.d_U) cb.d_U = dalloc<float>(n);
     if (!cb.d_gamma) cb.d_gamma = dalloc<float>(gamma.size());
     if (!ctx->s.vis2) ctx->s.vis2 = dalloc<float2>(ctx->s.vis_elems);
+    for (Lane& x : ctx->xl)
+      if (!x.s.vis2) x.s.vis2 = dalloc<float2>(ctx->s.vis_elems);
     upload(cb.d_U, U.data(), U.size(), st);
     upload(cb.d_gamma, gamma.data(), gamma.size(), st);
     FHS_CUDA(cudaStreamSynchronize(st));
@@ -1880,6 +2113,24 @@ fhs_status fhs_set_path(fhs_ctx* ctx, int32_t path) {
   });
 }
 
+fhs_status fhs_set_lanes(fhs_ctx* ctx, int32_t lanes) {
+  return guarded(ctx, [&] {
+    FHS_REQUIRE(lanes >= 1 && lanes <= kMaxLanes, FHS_ERR_INVALID_ARG, "lanes must be in [1, 4]");
+    if ((int)ctx->xl.size() + 1 > lanes) {
+      if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+      ctx->graph_key.clear();
+      free_lanes(ctx, lanes);
+    }
+    ctx->lanes = lanes;
+  });
+}
+
+fhs_status fhs_get_lanes(const fhs_ctx* ctx, int32_t* lanes) {
+  if (!ctx || !lanes) return FHS_ERR_INVALID_ARG;
+  *lanes = lanes_in_use(ctx);
+  return FHS_OK;
+}
+
 fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fhs_iter_stats* stats) {
   return guarded(ctx, [&] {
     FHS_REQUIRE(it && n_iter >= 0, FHS_ERR_INVALID_ARG, "bad arguments");
@@ -1888,6 +2139,7 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
     key.push_back((const void*)(intptr_t)ctx->path);
     key.push_back((const void*)(intptr_t)ctx->timer);
     key.push_back((const void*)(uintptr_t)ctx->param_version);
+    key.push_back((const void*)(intptr_t)ctx->lanes);
     for (int c = 0; c < nc; ++c) {
       const fhs_iterate& a = it[c];
       FHS_REQUIRE(a.X && a.Xcheck && a.y && a.state.W && a.state.theta && a.state.P && a.state.theta_bar &&
@@ -1906,6 +2158,7 @@ fhs_status fhs_pdfb_iter(fhs_ctx* ctx, const fhs_iterate* it, int32_t n_iter, fh
     if (!ctx->graph_exec || key != ctx->graph_key) {
       if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
       ensure_coef(ctx);   // no allocation may happen inside the capture
+      ensure_lanes(ctx);
       cudaStream_t user = ctx->stream;
       uint64_t before = g_launches.load();
       FHS_CUDA(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));

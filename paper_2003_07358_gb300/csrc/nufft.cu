@@ -362,7 +362,169 @@ static void col_n(const Cube& cb, float2* grid, int ngroups, int gmul, int istri
     default: break;                                  \
   }
 
+// ------------------------------------------------ mixed-radix transforms
+// Grid sides K = 2^a 3^b that are not powers of two (images of 3 * 2^m pixels): Stockham
+// autosort passes of radix 4, 2 and 3 between two shared-memory buffers holding W
+// interleaved sequences buf[n * W + w], twiddles exp(-2 pi i k / Kmax) from the
+// context's table (Kmax is a multiple of every grid side).  Rows: one CTA per image
+// row; columns: one CTA per W adjacent grid columns, the whole column in one pass, so
+// the grid rows stay in natural order (N1c = K1, N2c = 1).
+__device__ __forceinline__ void dft3(float2& x0, float2& x1, float2& x2, bool inv) {
+  const float h = 0.866025403784438646764f;                  // sqrt(3) / 2
+  const float2 t = cadd(x1, x2), d = csub(x1, x2);
+  const float2 m = make_float2(fmaf(-0.5f, t.x, x0.x), fmaf(-0.5f, t.y, x0.y));
+  const float2 ihd = make_float2(-h * d.y, h * d.x);         // i (sqrt(3) / 2) (x1 - x2)
+  x0 = cadd(x0, t);
+  // forward: y1 = m - i h d, y2 = m + i h d; the inverse flips the sign of i
+  x1 = inv ? cadd(m, ihd) : csub(m, ihd);
+  x2 = inv ? csub(m, ihd) : cadd(m, ihd);
+}
+
+template <int R>
+__device__ __forceinline__ void gen_pass(const float2* __restrict__ src, float2* __restrict__ dst, int N, int W,
+                                         int Ns, const float2* __restrict__ tw, int Kmax, bool inv) {
+  const int nb = (N / R) * W, tstep = Kmax / (Ns * R);
+  for (int item = threadIdx.x; item < nb; item += blockDim.x) {
+    const int w = item % W, j = item / W, k = j % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * (N / R)) * W + w];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 t = __ldg(&tw[(size_t)(r * k) * tstep]);
+        if (inv) t = cconj(t);
+        v[r] = cmul(v[r], t);
+      }
+    }
+    if constexpr (R == 2) dft2(v[0], v[1]);
+    else if constexpr (R == 3) dft3(v[0], v[1], v[2], inv);
+    else dft4(v[0], v[1], v[2], v[3], inv);
+    const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(base + r * Ns) * W + w] = v[r];
+  }
+}
+
+// Runs the passes of plan p on a (b is the other buffer); returns the buffer that holds
+// the transform.
+__device__ float2* gen_fft(float2* a, float2* b, const GenPlan& p, int W, const float2* __restrict__ tw, int Kmax,
+                           bool inv) {
+  int Ns = 1;
+  for (int q = 0; q < p.npass; ++q) {
+    const int R = p.radix[q];
+    if (R == 4) gen_pass<4>(a, b, p.n, W, Ns, tw, Kmax, inv);
+    else if (R == 3) gen_pass<3>(a, b, p.n, W, Ns, tw, Kmax, inv);
+    else gen_pass<2>(a, b, p.n, W, Ns, tw, Kmax, inv);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// Z then row DFT of image row blockIdx.x of channel blockIdx.y -> grid row (r - n1/2) mod K1.
+__global__ void __launch_bounds__(256) k_gen_row_fwd(const float* __restrict__ x, float2* __restrict__ grid,
+                                                     const float* __restrict__ sr, const float* __restrict__ sc,
+                                                     const GenPlan p, const float2* __restrict__ tw, int Kmax, int n1,
+                                                     int n2, int K1) {
+  extern __shared__ float2 gsm[];
+  const int r = blockIdx.x, l = blockIdx.y, N = p.n, h2 = n2 / 2;
+  const float* xr = x + ((size_t)l * n1 + r) * n2;
+  const float s_r = sr[r];
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const int c = n < h2 ? n + h2 : (n >= N - h2 ? n - (N - h2) : -1);
+    gsm[n] = make_float2(c >= 0 ? xr[c] * s_r * sc[c] : 0.f, 0.f);
+  }
+  __syncthreads();
+  const float2* res = gen_fft(gsm, gsm + N, p, 1, tw, Kmax, false);
+  float2* gr = grid + ((size_t)l * K1 + (r - n1 / 2 + K1) % K1) * N;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) gr[n] = res[n];
+}
+
+// Inverse row DFT of the grid row of image row blockIdx.x, then crop, Z^T, real part:
+// out[l][r][c] (+)= eta_l s_r s_c Re(...).
+__global__ void __launch_bounds__(256) k_gen_row_adj(const float2* __restrict__ grid, float* __restrict__ out,
+                                                     const float* __restrict__ sr, const float* __restrict__ sc,
+                                                     const float* __restrict__ eta, int accumulate, const GenPlan p,
+                                                     const float2* __restrict__ tw, int Kmax, int n1, int n2,
+                                                     int K1) {
+  extern __shared__ float2 gsm[];
+  const int r = blockIdx.x, l = blockIdx.y, N = p.n, h2 = n2 / 2;
+  const float2* gr = grid + ((size_t)l * K1 + (r - n1 / 2 + K1) % K1) * N;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) gsm[n] = gr[n];
+  __syncthreads();
+  const float2* res = gen_fft(gsm, gsm + N, p, 1, tw, Kmax, true);
+  const float e = (eta ? eta[l] : 1.f) * sr[r];
+  float* ol = out + ((size_t)l * n1 + r) * n2;
+  for (int c = threadIdx.x; c < n2; c += blockDim.x) {
+    const float val = e * sc[c] * res[(c - h2 + N) % N].x;
+    ol[c] = accumulate ? ol[c] + val : val;
+  }
+}
+
+// Column DFT (length K1 = p.n) of grid columns [c0, c0 + W) of channel blockIdx.y, in
+// natural row order.  Forward: rows outside the zero-padded image band read as zero;
+// inverse: only the rows of the band are stored (the crop keeps no others).
+__global__ void __launch_bounds__(256) k_gen_col(float2* __restrict__ grid, const GenPlan p, int W, int K2, int n1,
+                                                 int inv, const float2* __restrict__ tw, int Kmax) {
+  extern __shared__ float2 gsm[];
+  const int N = p.n, c0 = blockIdx.x * W, l = blockIdx.y, h1 = n1 / 2;
+  float2* gl = grid + (size_t)l * N * K2;
+  for (int idx = threadIdx.x; idx < N * W; idx += blockDim.x) {
+    const int i = idx / W, w = idx - i * W;
+    const bool zero = !inv && i >= h1 && i < N - h1;
+    gsm[idx] = zero ? make_float2(0.f, 0.f) : gl[(size_t)i * K2 + c0 + w];
+  }
+  __syncthreads();
+  const float2* res = gen_fft(gsm, gsm + N * W, p, W, tw, Kmax, inv != 0);
+  for (int idx = threadIdx.x; idx < N * W; idx += blockDim.x) {
+    const int i = idx / W, w = idx - i * W;
+    if (inv && i >= h1 && i < N - h1) continue;
+    gl[(size_t)i * K2 + c0 + w] = res[idx];
+  }
+}
+
+static int gen_col_width(int K1) { return K1 <= 1536 ? 8 : 4; }
+
+static void gen_smem_attrs() {
+  static bool attr = false;
+  if (attr) return;
+  cudaFuncSetAttribute(k_gen_row_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(k_gen_row_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(k_gen_col, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  attr = true;
+}
+
+static void launch_fft_forward_gen(fhs_ctx* ctx, const Cube& cb, const float* x, float2* grid, cudaStream_t st) {
+  gen_smem_attrs();
+  k_gen_row_fwd<<<dim3(cb.n1, cb.L), 256, 2 * (size_t)cb.K2 * sizeof(float2), st>>>(
+      x, grid, cb.d_scale_r, cb.d_scale_c, cb.plan_c, ctx->d_tw, ctx->Kmax, cb.n1, cb.n2, cb.K1);
+  const int W = gen_col_width(cb.K1);
+  k_gen_col<<<dim3(cb.K2 / W, cb.L), 256, 2 * (size_t)cb.K1 * W * sizeof(float2), st>>>(
+      grid, cb.plan_r, W, cb.K2, cb.n1, 0, ctx->d_tw, ctx->Kmax);
+  note_launches(2);
+}
+
+static void launch_fft_adjoint_gen(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta,
+                                   bool accumulate, cudaStream_t st) {
+  gen_smem_attrs();
+  const int W = gen_col_width(cb.K1);
+  k_gen_col<<<dim3(cb.K2 / W, cb.L), 256, 2 * (size_t)cb.K1 * W * sizeof(float2), st>>>(
+      grid, cb.plan_r, W, cb.K2, cb.n1, 1, ctx->d_tw, ctx->Kmax);
+  k_gen_row_adj<<<dim3(cb.n1, cb.L), 256, 2 * (size_t)cb.K2 * sizeof(float2), st>>>(
+      grid, out, cb.d_scale_r, cb.d_scale_c, eta, accumulate ? 1 : 0, cb.plan_c, ctx->d_tw, ctx->Kmax, cb.n1, cb.n2,
+      cb.K1);
+  note_launches(2);
+}
+
 void launch_fft_forward(fhs_ctx* ctx, const Cube& cb, const float* x, float2* grid, cudaStream_t st) {
+  if (!cb.pow2) {
+    launch_fft_forward_gen(ctx, cb, x, grid, st);
+    return;
+  }
   if (ctx->path == FHS_PATH_FAST) {
     launch_fft_forward_fast(ctx, cb, x, grid, st);
     return;
@@ -378,6 +540,10 @@ void launch_fft_forward(fhs_ctx* ctx, const Cube& cb, const float* x, float2* gr
 
 void launch_fft_adjoint(fhs_ctx* ctx, const Cube& cb, float2* grid, float* out, const float* eta, bool accumulate,
                         cudaStream_t st) {
+  if (!cb.pow2) {
+    launch_fft_adjoint_gen(ctx, cb, grid, out, eta, accumulate, st);
+    return;
+  }
   if (ctx->path == FHS_PATH_FAST) {
     launch_fft_adjoint_fast(ctx, cb, grid, out, eta, accumulate, st);
     return;
@@ -447,12 +613,23 @@ __device__ __forceinline__ int kb_weights(float om, float hi, float lo, float* w
 // --------------------------------------------------------- degridding G
 struct VisGeom {
   int K1, K2, N1c, N2c;
-  int lg1, lg2;          // log2(N1c), log2(N2c)
+  int lg1, lg2;          // log2(N1c), log2(N2c) (two-pass column transforms)
+  int pw;                // 1: K1 and K2 are powers of two (index wrap by masks)
   TapConst tc;
 };
 
-// Physical row of frequency row k (N1c, N2c powers of two): shifts, no division.
+// Grid index k in [-K, 2K) wrapped into [0, K): a mask for power-of-two grids, one
+// conditional add or subtract otherwise (K = 2^a 3^b).
+__device__ __forceinline__ int wrap_k(int k, int K, int pw) {
+  return pw ? (k & (K - 1)) : (k < 0 ? k + K : (k >= K ? k - K : k));
+}
+__device__ __forceinline__ int wrap1(int k, const VisGeom& vg) { return wrap_k(k, vg.K1, vg.pw); }
+__device__ __forceinline__ int wrap2(int k, const VisGeom& vg) { return wrap_k(k, vg.K2, vg.pw); }
+
+// Physical row of frequency row k: natural order after a one-pass column transform
+// (N2c = 1), else the two-pass digit-reversed order (N1c, N2c powers of two: shifts).
 __device__ __forceinline__ int phys_row2(int k, const VisGeom& vg) {
+  if (vg.N2c == 1) return k;
   return ((k & (vg.N1c - 1)) << vg.lg2) | (k >> vg.lg1);
 }
 
@@ -466,12 +643,12 @@ __device__ __forceinline__ float2 degrid_one(const float2* __restrict__ g, float
 #pragma unroll 1
   for (int a = 0; a < kTaps; ++a) {
     const float wra = kb_tap(a, xr);
-    int row = phys_row2((kr + a) & (vg.K1 - 1), vg);
+    int row = phys_row2(wrap1(kr + a, vg), vg);
     const float2* gr = g + (size_t)row * vg.K2;
     float2 racc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int b = 0; b < kTaps; ++b) {
-      float2 v = __ldg(&gr[(kc + b) & (vg.K2 - 1)]);
+      float2 v = __ldg(&gr[wrap2(kc + b, vg)]);
       racc.x = fmaf(wc[b], v.x, racc.x);
       racc.y = fmaf(wc[b], v.y, racc.y);
     }
@@ -621,11 +798,13 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
   const bool tma = staged && use_tma && tc + 1 < ntc;
   if (tma) {
     if (threadIdx.x == 0) {
-      const int k0 = tr * T, k1 = (tr * T + T) & (vg.K1 - 1);
+      const int k0 = tr * T, k1 = wrap1(tr * T + T, vg);
       mbar_init(&bar, 1);
       mbar_expect_tx(&bar, (unsigned)(R * SP * sizeof(float2)));
-      tma_load_4d(sg, &tm_rows, tc * T, k0 >> vg.lg1, k0 & (vg.N1c - 1), l, &bar);
-      tma_load_4d(sg + T * SP, &tm_halo, tc * T, k1 >> vg.lg1, k1 & (vg.N1c - 1), l, &bar);
+      // view coordinates (t, r) of frequency row k: physical row r N2c + t
+      const bool nat = vg.N2c == 1;
+      tma_load_4d(sg, &tm_rows, tc * T, nat ? 0 : k0 >> vg.lg1, nat ? k0 : k0 & (vg.N1c - 1), l, &bar);
+      tma_load_4d(sg + T * SP, &tm_halo, tc * T, nat ? 0 : k1 >> vg.lg1, nat ? k1 : k1 & (vg.N1c - 1), l, &bar);
     }
     __syncthreads();                       // the barrier is initialised before anyone waits
     mbar_wait(&bar, 0);
@@ -636,10 +815,10 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
     for (int c0 = 0; c0 < R; c0 += 32) {
       const int cc = c0 + lane;
       if (cc >= R) continue;
-      const int col = (tc * T + cc) & (vg.K2 - 1);
+      const int col = wrap2(tc * T + cc, vg);
 #pragma unroll 4
       for (int rr = wrp; rr < R; rr += 8) {
-        const int row = phys_row2((tr * T + rr) & (vg.K1 - 1), vg);
+        const int row = phys_row2(wrap1(tr * T + rr, vg), vg);
         const unsigned sa = (unsigned)__cvta_generic_to_shared(&sg[rr * SP + cc]);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gl + (size_t)row * vg.K2 + col));
       }
@@ -670,7 +849,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiled(const float2* __restrict__
       float wc[kTaps], xr;
       const int kr = kb_first(w.y, vg.tc.hi_r, vg.tc.lo_r, xr);
       const int kc = kb_weights(w.x, vg.tc.hi_c, vg.tc.lo_c, wc);
-      const int lr = (kr & (vg.K1 - 1)) - tr * T, lc = (kc & (vg.K2 - 1)) - tc * T;
+      const int lr = wrap1(kr, vg) - tr * T, lc = wrap2(kc, vg) - tc * T;
       // the host sort puts the first tap in this tile; anything else reads the grid directly
       if (staged && lr >= 0 && lr < T && lc >= 0 && lc < T) {
         const float2* sp = sg + lr * SP + lc;
@@ -1015,8 +1194,8 @@ __global__ void __launch_bounds__(kGridThreads, 1024 / kGridThreads) k_grid(cons
 #pragma unroll
       for (int a = 0; a < kTaps; ++a) ra[a] *= S;
       // footprint start in the source tile, relative to this tile
-      const int lr = (kr & (vg.K1 - 1)) - sr * T - dr * T;
-      const int lc = (kc & (vg.K2 - 1)) - sc * T - dc * T;
+      const int lr = wrap1(kr, vg) - sr * T - dr * T;
+      const int lc = wrap2(kc, vg) - sc * T - dc * T;
       if (k >= ibeg && k < iend) {
         grid_taps<true, MODE>(are, aim, TP, lr, lc, ra, wc, val.x, val.y, 0, kTaps, 0, kTaps);
       } else {
@@ -1055,6 +1234,7 @@ static VisGeom vis_geom(const Cube& cb) {
   vg.K1 = cb.K1; vg.K2 = cb.K2; vg.N1c = cb.N1c; vg.N2c = cb.N2c;
   vg.lg1 = __builtin_ctz(cb.N1c);
   vg.lg2 = __builtin_ctz(cb.N2c);
+  vg.pw = cb.pow2 ? 1 : 0;
   vg.tc = tap_const(cb.K1, cb.K2);
   return vg;
 }
@@ -1076,11 +1256,19 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 void encode_degrid_maps(fhs_ctx* ctx) {
-  for (Cube& cb : ctx->cubes) encode_cube_maps(cb, ctx->s.grid);
+  for (Cube& cb : ctx->cubes) encode_cube_maps(cb, ctx->s.grid, 0);
 }
 
-// TMA maps of cube cb's tile staging over the grid buffer `grid` ([L][K1][K2] float2).
-void encode_cube_maps(Cube& cb, const float2* grid) {
+// Slot of cube cb's TMA maps encoded over `grid`, or -1 (asynchronous copies).
+static int map_slot(const Cube& cb, const float2* grid) {
+  for (int k = 0; k < kMaxLanes; ++k)
+    if (cb.tm_grid[k] && cb.tm_grid[k] == grid) return k;
+  return -1;
+}
+
+// TMA maps (slot `slot`) of cube cb's tile staging over the grid buffer `grid`
+// ([L][K1][K2] float2).
+void encode_cube_maps(Cube& cb, const float2* grid, int slot) {
   static EncodeTiledFn encode = nullptr;
   static bool looked = false;
   if (!looked) {
@@ -1092,7 +1280,7 @@ void encode_cube_maps(Cube& cb, const float2* grid) {
       encode = (EncodeTiledFn)fn;
   }
   {
-    cb.tma = false;
+    cb.tm_grid[slot] = nullptr;
     const int T = cb.tile, S = degrid_stage_stride(T);
     // the tile rows must lie in one t-slice of the view and the box must fit the grid
     const bool geom = (cb.N2c == 1 || cb.N1c == T) && T + kTaps - 1 <= 256 && S <= 256 && S <= cb.K2 &&
@@ -1103,13 +1291,13 @@ void encode_cube_maps(Cube& cb, const float2* grid) {
     cuuint32_t box_rows[4] = {(cuuint32_t)S, 1, (cuuint32_t)T, 1};
     cuuint32_t box_halo[4] = {(cuuint32_t)S, 1, (cuuint32_t)(kTaps - 1), 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r1 = encode(&cb.tm_rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)grid, dims, strides,
+    CUresult r1 = encode(&cb.tm_rows[slot], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)grid, dims, strides,
                          box_rows, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    CUresult r2 = encode(&cb.tm_halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)grid, dims, strides,
+    CUresult r2 = encode(&cb.tm_halo[slot], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)grid, dims, strides,
                          box_halo, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    cb.tma = (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS);
+    if (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) cb.tm_grid[slot] = grid;
   }
 }
 
@@ -1155,10 +1343,11 @@ void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, 
   }
   if (tiled) {
     dim3 grd(degrid_tiled_parts(cb), cb.L);
+    const int ms = map_slot(cb, grid), k = ms < 0 ? 0 : ms;
     k_degrid_tiled<0><<<grd, 256, degrid_tiled_smem(cb), st>>>(grid, cb.d_uv, cb.d_tile_off, cb.d_vis_off,
                                                                vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, out,
                                                                nullptr, nullptr, nullptr, nullptr, cb.B, nullptr,
-                                                               cb.tm_rows, cb.tm_halo, cb.tma ? 1 : 0);
+                                                               cb.tm_rows[k], cb.tm_halo[k], ms >= 0 ? 1 : 0);
   } else {
     dim3 grd(degrid_parts(cb), cb.L);
     k_degrid<<<grd, 256, 0, st>>>(grid, cb.d_uv, out, cb.d_vis_off, vis_geom(cb));
@@ -1169,10 +1358,11 @@ void launch_degrid(const Cube& cb, const float2* grid, float2* out, bool tiled, 
 void launch_degrid_pdfb_tiled(const Cube& cb, const float2* grid, const float2* y, const float2* v, float2* d_out,
                               float2* u_prev, double* partials, cudaStream_t st) {
   dim3 grd(degrid_tiled_parts(cb), cb.L);
+  const int ms = map_slot(cb, grid), k = ms < 0 ? 0 : ms;
   k_degrid_tiled<1><<<grd, 256, degrid_tiled_smem(cb), st>>>(grid, cb.d_uv, cb.d_tile_off, cb.d_vis_off,
                                                              vis_geom(cb), cb.tile, cb.ntile_r, cb.ntile_c, d_out, y,
-                                                             v, u_prev, cb.d_blk, cb.B, partials, cb.tm_rows,
-                                                             cb.tm_halo, cb.tma ? 1 : 0);
+                                                             v, u_prev, cb.d_blk, cb.B, partials, cb.tm_rows[k],
+                                                             cb.tm_halo[k], ms >= 0 ? 1 : 0);
   note_launches(1);
 }
 

@@ -1,19 +1,22 @@
 // Fast SARA l2,1 dual (Algorithm 2 W update, Table 2 row 3) on GB300, included
 // at the end of sara.cu (it uses that file's c_filt filter table).
 //
-//   k_ana2<F>   : one (basis, level) of the analysis for a 32x32 coefficient
-//                 tile of one channel: the input tile with its filter halo is
-//                 staged in shared memory, filtered along x then y with
-//                 register blocking (each thread produces 4 outputs from one
-//                 window of F + 6 loaded values); writes the LL band for the
-//                 next level and the detail bands (/3) to the coefficient buffer.
+//   k_ana1_all  : level 1 of all eight bases for a 32x32 coefficient tile of one
+//                 channel from one staged db8 input window.
+//   k_ana2_all  : one level (2..4) of every basis in one launch, a 32x32
+//                 coefficient tile of one channel per CTA: the input tile with
+//                 its filter halo is staged in shared memory, filtered along x
+//                 then y with register blocking (each thread produces 4 outputs
+//                 from one window of F + 6 loaded values); writes the LL band for
+//                 the next level and the detail bands (/3) to the coefficient buffer.
 //   k_prox2     : the l2,1 dual over every coefficient of the sub-cube in one
 //                 streaming pass (Dirac block read straight from x):
 //                 W <- z min(1, alpha_i / ||z_i||), z = W + Psi^dagger x
 //                 (weights mode: theta_i = mu / (||Psi^dagger x||_i + mu)).
-//   k_syn2<F>   : one level (4 -> 2) of the synthesis of one basis for a 32x32
-//                 output tile of one channel, polyphase (even outputs take the
-//                 odd taps and vice versa), register-blocked.
+//   k_syn2_all  : one synthesis level (4 -> 3, 3 -> 2, 2 -> 1) of every basis in
+//                 one launch, a 32x32 output tile of one channel per CTA,
+//                 polyphase (even outputs take the odd taps and vice versa),
+//                 register-blocked.
 //   k_synfin    : level 1 of all eight bases and the Dirac block for a 32x32
 //                 output tile, accumulated in registers; A += kappa * result.
 // Same conventions as the plain kernels (zero-padded full convolution, odd
@@ -138,19 +141,56 @@ __device__ __forceinline__ void ana_stage(float (*tin)[kIn2 + 1], const float* _
   cp_async_wait<0>();
 }
 
-// One (basis, level) for a 32x32 coefficient tile of one channel.
+// One level (2, 3 or 4) of every basis in one launch: blockIdx.x runs over the
+// coefficient tiles of all bases (longest filters first), blockIdx.y over channels.
+// The bases of a level are independent (each reads its own coarser LL band), so one
+// launch per level replaces eight and the small levels fill the GPU together.
+struct Ana2Basis {
+  const float* in;     // LL band of the previous level [L][m1][m2]
+  float* ll_out;       // LL band of this level [L][mo1][mo2], or null: LL4 into coef (/3)
+  int64_t off[3];      // detail bands in the coefficient buffer
+  int64_t off_ll;      // LL4 (last level only)
+  int m1, m2, mo1, mo2;
+  int tiles_x;         // coefficient tiles along a row of this basis
+  int tile0;           // first linear tile of this basis
+  int F;               // filter length
+};
+struct Ana2All {
+  Ana2Basis b[8];
+  int nb;
+};
+
 template <int F>
-__global__ void __launch_bounds__(256) k_ana2(const float* __restrict__ in, float* __restrict__ ll_out,
-                                              float* __restrict__ coef, int64_t I, int64_t off0, int64_t off1,
-                                              int64_t off2, int64_t off_ll, int m1, int m2, int mo1, int mo2) {
+__device__ __forceinline__ void ana2_body(const Ana2Basis& B, int tile, int l, float* __restrict__ coef, int64_t I,
+                                          float (*tin)[kIn2 + 1], float (*tlx)[kT2 + 1], float (*thx)[kT2 + 1]) {
+  const int ty = tile / B.tiles_x, tx = tile - ty * B.tiles_x;
+  const int k0 = ty * kT2, c0 = tx * kT2;
+  ana_stage<2 * kT2 + F - 2>(tin, B.in + (size_t)l * B.m1 * B.m2, 2 * k0 + 2 - F, 2 * c0 + 2 - F, B.m1, B.m2);
+  ana_tile<F>(tin, 0, tlx, thx, coef + (size_t)l * I, B.ll_out ? B.ll_out + (size_t)l * B.mo1 * B.mo2 : nullptr,
+              B.off[0], B.off[1], B.off[2], B.off_ll, k0, c0, B.mo1, B.mo2);
+}
+
+__global__ void __launch_bounds__(256, 4) k_ana2_all(const Ana2All a, float* __restrict__ coef, int64_t I) {
   __shared__ float tin[kIn2][kIn2 + 1];
   __shared__ float tlx[kIn2][kT2 + 1];
   __shared__ float thx[kIn2][kT2 + 1];
-  const int l = blockIdx.z;
-  const int k0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
-  ana_stage<2 * kT2 + F - 2>(tin, in + (size_t)l * m1 * m2, 2 * k0 + 2 - F, 2 * c0 + 2 - F, m1, m2);
-  ana_tile<F>(tin, 0, tlx, thx, coef + (size_t)l * I, ll_out ? ll_out + (size_t)l * mo1 * mo2 : nullptr, off0, off1,
-              off2, off_ll, k0, c0, mo1, mo2);
+  const int t = blockIdx.x, l = blockIdx.y;
+  int bi = 0;
+#pragma unroll 1
+  for (int k = 1; k < a.nb; ++k)
+    if (t >= a.b[k].tile0) bi = k;
+  const Ana2Basis& B = a.b[bi];
+  const int tile = t - B.tile0;
+  switch (B.F) {
+    case 2: ana2_body<2>(B, tile, l, coef, I, tin, tlx, thx); break;
+    case 4: ana2_body<4>(B, tile, l, coef, I, tin, tlx, thx); break;
+    case 6: ana2_body<6>(B, tile, l, coef, I, tin, tlx, thx); break;
+    case 8: ana2_body<8>(B, tile, l, coef, I, tin, tlx, thx); break;
+    case 10: ana2_body<10>(B, tile, l, coef, I, tin, tlx, thx); break;
+    case 12: ana2_body<12>(B, tile, l, coef, I, tin, tlx, thx); break;
+    case 14: ana2_body<14>(B, tile, l, coef, I, tin, tlx, thx); break;
+    default: ana2_body<16>(B, tile, l, coef, I, tin, tlx, thx); break;
+  }
 }
 
 // Level 1 of all eight bases for a 32x32 coefficient tile of one channel: the input
@@ -231,12 +271,14 @@ struct Syn2 {
   int mo1, mo2, m1, m2;
 };
 
-constexpr int kTS2 = kKn2 * (kKn2 + 1);             // one staged band
+// Staging of the four coefficient bands (LL, d0, d1, d2; raw values, zero outside the
+// level) of the synthesis tile (r0, c0) of channel l: window rows [r0/2, r0/2 + KN),
+// columns [c0/2, c0/2 + KN), KN = 16 + F/2, by 4-byte asynchronous copies (lane =
+// column, warp = row), band b at b kTS2e, rows at stride kKn2 + 1.
+constexpr int kTS2e = kKn2 * (kKn2 + 1);             // 600
 
-// Stage the four coefficient bands (LL, d0, d1, d2; raw values, zero outside the
-// level) of the output tile (r0, c0) of channel l into tc[4][kKn2][kKn2+1].
 template <int F>
-__device__ __forceinline__ void syn2_stage(const Syn2& s, int l, int r0, int c0, float* tc) {
+__device__ __forceinline__ void syn2_stage_e(const Syn2& s, int l, int r0, int c0, float* tc) {
   constexpr int KN = kT2 / 2 + F / 2;
   static_assert(KN <= 32, "one warp spans a staged row");
   const int kc = threadIdx.x & 31, kr0 = threadIdx.x >> 5;   // lane = column, warp = row (step 8)
@@ -256,7 +298,7 @@ __device__ __forceinline__ void syn2_stage(const Syn2& s, int l, int r0, int c0,
       for (int j = 0; j < (KN + 7) / 8; ++j) {
         if (kr0 + 8 * j < KN) {
           const bool v = j < nrows;
-          cp_async4(dst + band * kTS2 + 8 * j * (kKn2 + 1), v ? src : b0, v);
+          cp_async4(dst + band * kTS2e + 8 * j * (kKn2 + 1), v ? src : b0, v);
         }
         src += step;
       }
@@ -266,10 +308,12 @@ __device__ __forceinline__ void syn2_stage(const Syn2& s, int l, int r0, int c0,
 }
 
 // Synthesis of one staged (basis, level) tile, added to acc[4]: outputs at row
-// il = threadIdx.x >> 3, columns 4 * (threadIdx.x & 7) + q.  Coefficients carry
-// the 1/3 of the dictionary except a synthesised LL band (ll_scale = 1).
-template <int F>
-__device__ __forceinline__ void syn2_compute(const float* tc, float* lx, float* hx, float ll_scale, float acc[4]) {
+// il = threadIdx.x >> 3, columns 4 * (threadIdx.x & 7) + q.  tl, t0, t1, t2: window
+// element (0, 0) of the LL, d0, d1, d2 bands, rows at stride R.  Coefficients carry the
+// 1/3 of the dictionary except a synthesised LL band (ll_scale = 1).
+template <int F, int R>
+__device__ __forceinline__ void syn2_compute(const float* tl, const float* t0, const float* t1, const float* t2,
+                                             float* lx, float* hx, float ll_scale, float acc[4]) {
   constexpr int KN = kT2 / 2 + F / 2;
   constexpr int WIN = F / 2 + 1;
   FTaps<F> f;
@@ -280,11 +324,11 @@ __device__ __forceinline__ void syn2_compute(const float* tc, float* lx, float* 
     float vl[WIN + 1], v1[WIN + 1], v0[WIN + 1], v2[WIN + 1];
 #pragma unroll
     for (int u = 0; u <= WIN; ++u) {
-      const int o = (mg + u) * (kKn2 + 1) + kc;
-      vl[u] = tc[o];
-      v0[u] = tc[kTS2 + o];
-      v1[u] = tc[2 * kTS2 + o];
-      v2[u] = tc[3 * kTS2 + o];
+      const int o = (mg + u) * R + kc;
+      vl[u] = tl[o];
+      v0[u] = t0[o];
+      v1[u] = t1[o];
+      v2[u] = t2[o];
     }
     // raw coefficients; the dictionary's 1/3 (and ll_scale) applied once per output
 #pragma unroll
@@ -331,43 +375,59 @@ __device__ __forceinline__ void syn2_compute(const float* tc, float* lx, float* 
   __syncthreads();
 }
 
+// Staging and compute of basis b = F/2 - 1 (runtime b, compile-time F).
 __device__ __forceinline__ void syn2_stage_any(int b, const Syn2& s, int l, int r0, int c0, float* tc) {
   switch (b) {
-    case 0: syn2_stage<2>(s, l, r0, c0, tc); break;
-    case 1: syn2_stage<4>(s, l, r0, c0, tc); break;
-    case 2: syn2_stage<6>(s, l, r0, c0, tc); break;
-    case 3: syn2_stage<8>(s, l, r0, c0, tc); break;
-    case 4: syn2_stage<10>(s, l, r0, c0, tc); break;
-    case 5: syn2_stage<12>(s, l, r0, c0, tc); break;
-    case 6: syn2_stage<14>(s, l, r0, c0, tc); break;
-    default: syn2_stage<16>(s, l, r0, c0, tc); break;
+    case 0: syn2_stage_e<2>(s, l, r0, c0, tc); break;
+    case 1: syn2_stage_e<4>(s, l, r0, c0, tc); break;
+    case 2: syn2_stage_e<6>(s, l, r0, c0, tc); break;
+    case 3: syn2_stage_e<8>(s, l, r0, c0, tc); break;
+    case 4: syn2_stage_e<10>(s, l, r0, c0, tc); break;
+    case 5: syn2_stage_e<12>(s, l, r0, c0, tc); break;
+    case 6: syn2_stage_e<14>(s, l, r0, c0, tc); break;
+    default: syn2_stage_e<16>(s, l, r0, c0, tc); break;
   }
+}
+
+template <int F>
+__device__ __forceinline__ void syn2_compute_e(const float* tc, float* lx, float* hx, float lls, float acc[4]) {
+  syn2_compute<F, kKn2 + 1>(tc, tc + kTS2e, tc + 2 * kTS2e, tc + 3 * kTS2e, lx, hx, lls, acc);
 }
 
 __device__ __forceinline__ void syn2_compute_any(int b, const float* tc, float* lx, float* hx, float lls,
                                                  float acc[4]) {
   switch (b) {
-    case 0: syn2_compute<2>(tc, lx, hx, lls, acc); break;
-    case 1: syn2_compute<4>(tc, lx, hx, lls, acc); break;
-    case 2: syn2_compute<6>(tc, lx, hx, lls, acc); break;
-    case 3: syn2_compute<8>(tc, lx, hx, lls, acc); break;
-    case 4: syn2_compute<10>(tc, lx, hx, lls, acc); break;
-    case 5: syn2_compute<12>(tc, lx, hx, lls, acc); break;
-    case 6: syn2_compute<14>(tc, lx, hx, lls, acc); break;
-    default: syn2_compute<16>(tc, lx, hx, lls, acc); break;
+    case 0: syn2_compute_e<2>(tc, lx, hx, lls, acc); break;
+    case 1: syn2_compute_e<4>(tc, lx, hx, lls, acc); break;
+    case 2: syn2_compute_e<6>(tc, lx, hx, lls, acc); break;
+    case 3: syn2_compute_e<8>(tc, lx, hx, lls, acc); break;
+    case 4: syn2_compute_e<10>(tc, lx, hx, lls, acc); break;
+    case 5: syn2_compute_e<12>(tc, lx, hx, lls, acc); break;
+    case 6: syn2_compute_e<14>(tc, lx, hx, lls, acc); break;
+    default: syn2_compute_e<16>(tc, lx, hx, lls, acc); break;
   }
 }
 
+// One synthesis level (4 -> 3, 3 -> 2 or 2 -> 1) of every basis in one launch, tiles of
+// all bases along blockIdx.x (longest filters first), channels along blockIdx.y.
+struct Syn2All {
+  Syn2 s[8];
+  float* out[8];       // synthesised LL band of the finer level [L][m1][m2]
+  int tiles_x[8], tile0[8], F[8];
+  int nb;
+};
+
 template <int F>
-__global__ void __launch_bounds__(256) k_syn2(Syn2 s, float* __restrict__ out) {
-  __shared__ float sh[4 * kTS2 + 2 * kT2 * (kKn2 + 1)];
-  const int l = blockIdx.z;
-  const int r0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
+__device__ __forceinline__ void syn2_body(const Syn2& s, float* __restrict__ out, int tiles_x, int tile, int l,
+                                          float* sh) {
+  const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+  const int r0 = ty * kT2, c0 = tx * kT2;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  syn2_stage<F>(s, l, r0, c0, sh);
+  syn2_stage_e<F>(s, l, r0, c0, sh);
   cp_async_wait<0>();
   __syncthreads();
-  syn2_compute<F>(sh, sh + 4 * kTS2, sh + 4 * kTS2 + kT2 * (kKn2 + 1), s.ll ? 1.f : 1.f / 3.f, acc);
+  syn2_compute<F, kKn2 + 1>(sh, sh + kTS2e, sh + 2 * kTS2e, sh + 3 * kTS2e, sh + 4 * kTS2e,
+                            sh + 4 * kTS2e + kT2 * (kKn2 + 1), s.ll ? 1.f : 1.f / 3.f, acc);
   const int il = threadIdx.x >> 3, jc0 = 4 * (threadIdx.x & 7);
   const int r = r0 + il;
   if (r >= s.m1) return;
@@ -375,6 +435,26 @@ __global__ void __launch_bounds__(256) k_syn2(Syn2 s, float* __restrict__ out) {
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     if (c0 + jc0 + q < s.m2) ol[c0 + jc0 + q] = acc[q];
+}
+
+__global__ void __launch_bounds__(256) k_syn2_all(const Syn2All a) {
+  __shared__ float sh[4 * kTS2e + 2 * kT2 * (kKn2 + 1)];
+  const int t = blockIdx.x, l = blockIdx.y;
+  int bi = 0;
+#pragma unroll 1
+  for (int k = 1; k < a.nb; ++k)
+    if (t >= a.tile0[k]) bi = k;
+  const int tile = t - a.tile0[bi];
+  switch (a.F[bi]) {
+    case 2: syn2_body<2>(a.s[bi], a.out[bi], a.tiles_x[bi], tile, l, sh); break;
+    case 4: syn2_body<4>(a.s[bi], a.out[bi], a.tiles_x[bi], tile, l, sh); break;
+    case 6: syn2_body<6>(a.s[bi], a.out[bi], a.tiles_x[bi], tile, l, sh); break;
+    case 8: syn2_body<8>(a.s[bi], a.out[bi], a.tiles_x[bi], tile, l, sh); break;
+    case 10: syn2_body<10>(a.s[bi], a.out[bi], a.tiles_x[bi], tile, l, sh); break;
+    case 12: syn2_body<12>(a.s[bi], a.out[bi], a.tiles_x[bi], tile, l, sh); break;
+    case 14: syn2_body<14>(a.s[bi], a.out[bi], a.tiles_x[bi], tile, l, sh); break;
+    default: syn2_body<16>(a.s[bi], a.out[bi], a.tiles_x[bi], tile, l, sh); break;
+  }
 }
 
 struct SynFin2 {
@@ -388,8 +468,8 @@ struct SynFin2 {
 // Level 1 of all bases: the tiles of basis b + 1 are staged (cp.async) while basis b
 // is computed.
 __global__ void __launch_bounds__(256, 3) k_synfin(SynFin2 s, float* __restrict__ A) {
-  __shared__ float sh[2 * 4 * kTS2 + 2 * kT2 * (kKn2 + 1)];
-  float* lx = sh + 8 * kTS2;
+  __shared__ float sh[2 * 4 * kTS2e + 2 * kT2 * (kKn2 + 1)];
+  float* lx = sh + 8 * kTS2e;
   float* hx = lx + kT2 * (kKn2 + 1);
   const int l = blockIdx.z;
   const int r0 = blockIdx.y * kT2, c0 = blockIdx.x * kT2;
@@ -398,13 +478,13 @@ __global__ void __launch_bounds__(256, 3) k_synfin(SynFin2 s, float* __restrict_
 #pragma unroll 1
   for (int b = 0; b < 8; ++b) {
     if (b + 1 < 8) {
-      syn2_stage_any(b + 1, s.lv[b + 1], l, r0, c0, sh + ((b + 1) & 1) * 4 * kTS2);
+      syn2_stage_any(b + 1, s.lv[b + 1], l, r0, c0, sh + ((b + 1) & 1) * 4 * kTS2e);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    syn2_compute_any(b, sh + (b & 1) * 4 * kTS2, lx, hx, 1.f, acc);
+    syn2_compute_any(b, sh + (b & 1) * 4 * kTS2e, lx, hx, 1.f, acc);
   }
   const int il = threadIdx.x >> 3, jc0 = 4 * (threadIdx.x & 7);
   const int r = r0 + il;
@@ -432,34 +512,6 @@ __global__ void __launch_bounds__(256, 3) k_synfin(SynFin2 s, float* __restrict_
 }
 
 // ------------------------------------------------------------- launchers
-template <int F>
-static void ana2_launch(const Cube& cb, int b, int j, const float* in, float* ll_out, float* coef, cudaStream_t st) {
-  const SaraLayout& S = cb.sara;
-  dim3 g((S.cols[b][j] + kT2 - 1) / kT2, (S.rows[b][j] + kT2 - 1) / kT2, cb.L);
-  k_ana2<F><<<g, 256, 0, st>>>(in, ll_out, coef, S.I, S.off[b][j][0], S.off[b][j][1], S.off[b][j][2],
-                               S.off[b][kLevels][3], S.rows[b][j - 1], S.cols[b][j - 1], S.rows[b][j], S.cols[b][j]);
-  note_launches(1);
-}
-
-template <int F>
-static void syn2_launch(const Cube& cb, const Syn2& s, float* out, cudaStream_t st) {
-  dim3 g((s.m2 + kT2 - 1) / kT2, (s.m1 + kT2 - 1) / kT2, cb.L);
-  k_syn2<F><<<g, 256, 0, st>>>(s, out);
-  note_launches(1);
-}
-
-#define FHS_BASIS_SWITCH(b, FN, ...)              \
-  switch (b) {                                    \
-    case 0: FN<2>(__VA_ARGS__); break;            \
-    case 1: FN<4>(__VA_ARGS__); break;            \
-    case 2: FN<6>(__VA_ARGS__); break;            \
-    case 3: FN<8>(__VA_ARGS__); break;            \
-    case 4: FN<10>(__VA_ARGS__); break;           \
-    case 5: FN<12>(__VA_ARGS__); break;           \
-    case 6: FN<14>(__VA_ARGS__); break;           \
-    default: FN<16>(__VA_ARGS__); break;          \
-  }
-
 // Analysis of every basis and level into the coefficient buffer, the l2,1 dual (or
 // weights), then (dual mode) the synthesis accumulated into A.
 void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, const float* theta, float* A,
@@ -467,14 +519,16 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
   const SaraLayout& S = cb.sara;
   const int L = cb.L;
   float* coef = ctx->s.coef;
-  float* llA = ctx->s.t2;
-  float* llB = ctx->s.t3;
-  // LL1 slots of the eight bases (also read by the synthesis below)
+  // LL1, LL2 and LL3 slots of the eight bases (also used by the synthesis below)
   {
-    int64_t off = 0;
+    int64_t o1 = 0, o2 = 0, o3 = 0;
     for (int b = 0; b < 8; ++b) {
-      ctx->s.ll1_off[b] = off;
-      off += (int64_t)L * S.rows[b][1] * S.cols[b][1];
+      ctx->s.ll1_off[b] = o1;
+      ctx->s.ll2_off[b] = o2;
+      ctx->s.ll3_off[b] = o3;
+      o1 += (int64_t)L * S.rows[b][1] * S.cols[b][1];
+      o2 += (int64_t)L * S.rows[b][2] * S.cols[b][2];
+      o3 += (int64_t)L * S.rows[b][3] * S.cols[b][3];
     }
   }
   // level 1 of every basis in one launch (grid over the longest filter's coefficients)
@@ -492,13 +546,29 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
     k_ana1_all<<<g, 256, 0, st>>>(x, coef, ctx->s.ll1, a, S.I, cb.n1, cb.n2);
     note_launches(1);
   }
-  for (int b = 0; b < 8; ++b) {
-    const float* in = ctx->s.ll1 + ctx->s.ll1_off[b];
-    for (int j = 2; j <= kLevels; ++j) {
-      float* llo = (j == kLevels) ? nullptr : ((j & 1) ? llA : llB);
-      FHS_BASIS_SWITCH(b, ana2_launch, cb, b, j, in, llo, coef, st);
-      in = llo;
+  // levels 2..4: one launch per level over the tiles of every basis (longest filters
+  // first); LL2 and LL3 of each basis in its own slot of s.ll2 / s.ll3
+  for (int j = 2; j <= kLevels; ++j) {
+    Ana2All a;
+    a.nb = 8;
+    int t0 = 0;
+    for (int k = 0; k < 8; ++k) {
+      const int b = 7 - k;
+      Ana2Basis& B = a.b[k];
+      B.in = (j == 2) ? ctx->s.ll1 + ctx->s.ll1_off[b] : (j == 3) ? ctx->s.ll2 + ctx->s.ll2_off[b]
+                                                                  : ctx->s.ll3 + ctx->s.ll3_off[b];
+      B.ll_out = (j == 2) ? ctx->s.ll2 + ctx->s.ll2_off[b] : (j == 3) ? ctx->s.ll3 + ctx->s.ll3_off[b] : nullptr;
+      for (int q = 0; q < 3; ++q) B.off[q] = S.off[b][j][q];
+      B.off_ll = S.off[b][kLevels][3];
+      B.m1 = S.rows[b][j - 1]; B.m2 = S.cols[b][j - 1];
+      B.mo1 = S.rows[b][j]; B.mo2 = S.cols[b][j];
+      B.tiles_x = (B.mo2 + kT2 - 1) / kT2;
+      B.tile0 = t0;
+      B.F = 2 * (b + 1);
+      t0 += B.tiles_x * ((B.mo1 + kT2 - 1) / kT2);
     }
+    k_ana2_all<<<dim3(t0, L), 256, 0, st>>>(a, coef, S.I);
+    note_launches(1);
   }
   {
     const int64_t N = (int64_t)cb.n1 * cb.n2;
@@ -517,21 +587,33 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
   if (weights) return;
   SynFin2 fin;
   float* slots = ctx->s.ll1;
-  for (int b = 0; b < 8; ++b) {
-    const float* ll = nullptr;
-    for (int j = kLevels; j >= 2; --j) {
-      Syn2 s;
-      s.ll = ll;
+  // levels 4 -> 2: one launch per level over the tiles of every basis; the synthesised
+  // LL3, LL2 and LL1 bands reuse the analysis slots (s.ll3, s.ll2, s.ll1)
+  for (int j = kLevels; j >= 2; --j) {
+    Syn2All a;
+    a.nb = 8;
+    int t0 = 0;
+    for (int k = 0; k < 8; ++k) {
+      const int b = 7 - k;
+      Syn2& s = a.s[k];
+      s.ll = (j == kLevels) ? nullptr : (j == 3) ? ctx->s.ll3 + ctx->s.ll3_off[b] : ctx->s.ll2 + ctx->s.ll2_off[b];
       s.W = W;
       s.I = S.I;
       s.off[0] = S.off[b][j][0]; s.off[1] = S.off[b][j][1]; s.off[2] = S.off[b][j][2];
       s.off[3] = S.off[b][kLevels][3];
       s.mo1 = S.rows[b][j]; s.mo2 = S.cols[b][j];
       s.m1 = S.rows[b][j - 1]; s.m2 = S.cols[b][j - 1];
-      float* out = (j == 2) ? slots + ctx->s.ll1_off[b] : ((j & 1) ? llA : llB);
-      FHS_BASIS_SWITCH(b, syn2_launch, cb, s, out, st);
-      ll = out;
+      a.out[k] = (j == 2) ? slots + ctx->s.ll1_off[b] : (j == 3) ? ctx->s.ll2 + ctx->s.ll2_off[b]
+                                                                 : ctx->s.ll3 + ctx->s.ll3_off[b];
+      a.tiles_x[k] = (s.m2 + kT2 - 1) / kT2;
+      a.tile0[k] = t0;
+      a.F[k] = 2 * (b + 1);
+      t0 += a.tiles_x[k] * ((s.m1 + kT2 - 1) / kT2);
     }
+    k_syn2_all<<<dim3(t0, L), 256, 0, st>>>(a);
+    note_launches(1);
+  }
+  for (int b = 0; b < 8; ++b) {
     Syn2& f = fin.lv[b];
     f.ll = slots + ctx->s.ll1_off[b];
     f.W = W;

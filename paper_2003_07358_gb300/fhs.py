@@ -29,6 +29,7 @@ SYMBOLS = [
     "fhs_kernel_timer_read", "fhs_solve", "fhs_heuristic_params", "fhs_set_preconditioning",
     "fhs_pdfb_iter_host", "fhs_set_wait_limit", "fhs_set_alloc_limit",
     "fhs_checkpoint_save", "fhs_checkpoint_load", "fhs_set_dde", "fhs_set_autotune", "fhs_get_tuning",
+    "fhs_set_lanes", "fhs_get_lanes",
 ]
 MAX_SOLVE_CYCLES = 32
 FHS_PATH = {"fast": 0, "plain": 1}
@@ -133,6 +134,8 @@ def load(path: str = LIB_PATH):
         "fhs_set_dde": ([vp, i32, i32, i32, C.POINTER(C.c_float), C.POINTER(C.c_int32)], i32),
         "fhs_set_autotune": ([i32, C.c_char_p], i32),
         "fhs_get_tuning": ([vp, i32, C.POINTER(fhs_tuning)], i32),
+        "fhs_set_lanes": ([vp, i32], i32),
+        "fhs_get_lanes": ([vp, C.POINTER(i32)], i32),
         "fhs_pdfb_iter_host": ([vp, C.POINTER(fhs_iterate), C.POINTER(vp), C.POINTER(vp), i32,
                                 C.POINTER(fhs_iter_stats)], i32),
     }
@@ -424,6 +427,14 @@ class Context:
         return {"grid_tile": t.grid_tile, "degrid_tiled": t.degrid_tiled, "gram_tc": t.gram_tc,
                 "sara_fast": t.sara_fast, "prox_ctas_per_sm": t.prox_ctas_per_sm,
                 "source": {0: "defaults", 1: "measured", 2: "cache"}[t.source], "ms": list(t.ms)}
+
+    def fhs_set_lanes(self, lanes: int) -> None:
+        self._check(self.lib.fhs_set_lanes(self.h, lanes))
+
+    def fhs_get_lanes(self) -> int:
+        v = C.c_int32(0)
+        self._check(self.lib.fhs_get_lanes(self.h, C.byref(v)))
+        return v.value
 
     def fhs_set_dde(self, cube, kern=None, kidx=None):
         """DDE-extended de-gridding kernels: kern [n_kern][S_d][S_d] complex (first index

@@ -94,3 +94,34 @@ def test_batch_graph_replays_match_single_cube_contexts(batch):
         one.fhs_pdfb_iter(it1, 3, want_stats=False)
         assert torch.equal(X, its[c]["X"]), c
         one.close()
+
+
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_lanes_equal_one_lane_bit_for_bit(batch, lanes):
+    """fhs_set_lanes: the cubes dealt to further lanes (own streams and scratch, run
+    beside the first lane inside the iteration graph) give the same iterates, bit for
+    bit, as one lane; the lane count is reported."""
+    probs, ctx = batch
+
+    def run(lanes):
+        ctx.fhs_set_lanes(lanes)
+        its = []
+        for c, p in enumerate(probs):
+            X = torch.zeros((p.L, p.n1, p.n2), device="cuda")
+            u = torch.as_tensor(np.ascontiguousarray(p.y, dtype=np.complex64), device="cuda")
+            y = torch.empty_like(u)
+            ctx.fhs_vis_to_internal(c, u, y)
+            its.append({"X": X, "Xcheck": torch.zeros_like(X), "y": y, "state": ctx.new_state(c)})
+        stats = ctx.fhs_pdfb_iter(its, 3)
+        return its, stats, ctx.fhs_get_lanes()
+
+    two, st2, n2 = run(lanes)
+    one, st1, n1 = run(1)
+    assert (n2, n1) == (lanes, 1)
+    for c in range(len(probs)):
+        assert torch.equal(two[c]["X"], one[c]["X"]), c
+        assert torch.equal(two[c]["state"]["W"], one[c]["state"]["W"]), c
+        assert torch.equal(two[c]["state"]["v"], one[c]["state"]["v"]), c
+        assert st2[c] == st1[c], c
+    with pytest.raises(Exception):
+        ctx.fhs_set_lanes(5)

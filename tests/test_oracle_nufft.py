@@ -34,7 +34,7 @@ def test_taps_cover_support():
     assert np.all(w > 0)
 
 
-@pytest.mark.parametrize("n1,n2,M", [(32, 32, 300), (64, 64, 400), (48, 32, 250)])
+@pytest.mark.parametrize("n1,n2,M", [(32, 32, 300), (64, 64, 400), (48, 32, 250), (96, 48, 300)])
 def test_nufft_matches_direct_dft(n1, n2, M):
     rng = np.random.default_rng(n1 * 7 + n2)
     x = rng.random((n1, n2))
