@@ -298,9 +298,10 @@ def batch_measurement(args, torch, log) -> dict:
     sides included; 8..48 channels; 1..6 facets a side; 0.3..2 visibilities per pixel) in
     one context, one CUDA graph per iteration over all of them.  Data y = Phi x + noise
     formed with the library; parameters from the noise levels on the device
-    (fhs_heuristic_params).  Times 1, 2 and 4 lanes (fhs_set_lanes) and reports the
-    iterations per second of the whole batch with the fastest, and the launch choices
-    per shape."""
+    (fhs_heuristic_params); the launch choices of every shape measured by the autotuner
+    when the context is created.  Times 1, 2 and 4 lanes (fhs_set_lanes) and reports the
+    iterations per second of the whole batch with the fastest, and the choices per
+    cube."""
     from paper_2003_07358_gb300.fhs import Context, CubeParams
     specs = fs.batch_specs()
     cps, skies = [], []
@@ -317,9 +318,18 @@ def batch_measurement(args, torch, log) -> dict:
                               window=spec.window, M_lb=M_lb, uv=uv, eta=np.ones(spec.L), mu=0.0,
                               mu_bar=np.zeros(spec.Q * spec.Q), eps=np.zeros((spec.L, spec.B))))
         skies.append((sources, chans, M_lb))
+    # the launch choices of every shape measured in fhs_create (autotuner, mode 2), then
+    # the bench's own setting again
+    from paper_2003_07358_gb300.fhs import fhs_set_autotune
+    fhs_set_autotune(2, os.path.join(tempfile.gettempdir(), "fhs_autotune_batch.json"))
     t0 = time.time()
-    ctx = Context(cps)
-    log(f"batch context ({len(specs)} cubes) created in {time.time() - t0:.1f} s")
+    try:
+        ctx = Context(cps)
+    finally:
+        fhs_set_autotune(args.autotune, os.path.join(tempfile.gettempdir(), "fhs_autotune_rank0.json")
+                         if args.autotune else None)
+    ctx_s = time.time() - t0
+    log(f"batch context ({len(specs)} cubes, autotuned) created in {ctx_s:.1f} s")
     dev = ctx.device
     gen = torch.Generator(device=dev)
     its = []
@@ -377,7 +387,7 @@ def batch_measurement(args, torch, log) -> dict:
            "cubes": len(specs), "pixel_channels": int(sum(sp.n * sp.n * sp.L for sp in specs)),
            "visibilities": int(sum(sp.M * sp.L for sp in specs)), "ms_per_iteration": round(ms, 3),
            "iter_per_s": round(1000.0 / ms, 3), "lanes": ctx.fhs_get_lanes(), "timed_iterations": k,
-           "ms_per_iteration_by_lanes": lane_ms,
+           "ms_per_iteration_by_lanes": lane_ms, "context_and_autotune_s": round(ctx_s, 1),
            "xi_last": [round(s_["xi"], 6) for s_ in st], "choices_by_cube": tuning}
     ctx.close()
     log(f"batch: {ms:.2f} ms per iteration")

@@ -251,12 +251,32 @@ __global__ void __launch_bounds__(32) k_eig(const double* __restrict__ part, int
   const NucFacet f = facets[q];
   const int Nq = (f.r1 - f.r0) * (f.c1 - f.c0);
   const int nch = (Nq + kGramChunk - 1) / kGramChunk;
-  for (int idx = lane; idx < L * L; idx += 32) {
-    double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += part[((size_t)q * nchunk_max + c) * L * L + idx];
-    int a = idx / L, b = idx % L;
-    G[a * Ls + b] = s;
-    V[a * Ls + b] = (a == b) ? 1.0 : 0.0;
+  // sum of the chunk partials, chunk 0 first: eight entries of the lane at a time, so
+  // that each chunk's eight loads are in flight together (the order of the additions of
+  // an entry is the chunk order either way)
+  constexpr int kEigBatch = 8;
+  for (int e0 = lane; e0 < L * L; e0 += 32 * kEigBatch) {
+    double s[kEigBatch];
+#pragma unroll
+    for (int k = 0; k < kEigBatch; ++k) s[k] = 0.0;
+    const double* pq = part + (size_t)q * nchunk_max * L * L;
+    for (int c = 0; c < nch; ++c) {
+      const double* pc = pq + (size_t)c * L * L;
+#pragma unroll
+      for (int k = 0; k < kEigBatch; ++k) {
+        const int idx = e0 + 32 * k;
+        if (idx < L * L) s[k] += pc[idx];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kEigBatch; ++k) {
+      const int idx = e0 + 32 * k;
+      if (idx < L * L) {
+        const int a = idx / L, b = idx % L;
+        G[a * Ls + b] = s[k];
+        V[a * Ls + b] = (a == b) ? 1.0 : 0.0;
+      }
+    }
   }
   __syncwarp();
   // symmetrise (the partial Grams are symmetric up to rounding order)
