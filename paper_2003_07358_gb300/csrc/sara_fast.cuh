@@ -3,7 +3,8 @@
 //
 //   k_ana1_all  : level 1 of all eight bases for a 32x32 coefficient tile of one
 //                 channel from one staged db8 input window.
-//   k_ana2_all  : one level (2..4) of every basis in one launch, a 32x32
+//   k_ana2_all  : one level (2..4) of every basis in one launch (k_ana2_one: one
+//                 basis, for levels whose every basis fills the GPU alone), a 32x32
 //                 coefficient tile of one channel per CTA: the input tile with
 //                 its filter halo is staged in shared memory, filtered along x
 //                 then y with register blocking (each thread produces 4 outputs
@@ -14,7 +15,8 @@
 //                 W <- z min(1, alpha_i / ||z_i||), z = W + Psi^dagger x
 //                 (weights mode: theta_i = mu / (||Psi^dagger x||_i + mu)).
 //   k_syn2_all  : one synthesis level (4 -> 3, 3 -> 2, 2 -> 1) of every basis in
-//                 one launch, a 32x32 output tile of one channel per CTA,
+//                 one launch (k_syn2_one: one basis, as above), a 32x32 output
+//                 tile of one channel per CTA,
 //                 polyphase (even outputs take the odd taps and vice versa),
 //                 register-blocked.
 //   k_synfin    : level 1 of all eight bases and the Dirac block for a 32x32
@@ -191,6 +193,17 @@ __global__ void __launch_bounds__(256, 4) k_ana2_all(const Ana2All a, float* __r
     case 14: ana2_body<14>(B, tile, l, coef, I, tin, tlx, thx); break;
     default: ana2_body<16>(B, tile, l, coef, I, tin, tlx, thx); break;
   }
+}
+
+// One basis of a level on its own (tiles along blockIdx.x, channels along blockIdx.y):
+// used when every basis's tiles fill the GPU by themselves, where the per-filter
+// register allocation keeps more CTAs per SM than the merged kernel.
+template <int F>
+__global__ void __launch_bounds__(256) k_ana2_one(const Ana2Basis B, float* __restrict__ coef, int64_t I) {
+  __shared__ float tin[kIn2][kIn2 + 1];
+  __shared__ float tlx[kIn2][kT2 + 1];
+  __shared__ float thx[kIn2][kT2 + 1];
+  ana2_body<F>(B, blockIdx.x, blockIdx.y, coef, I, tin, tlx, thx);
 }
 
 // Level 1 of all eight bases for a 32x32 coefficient tile of one channel: the input
@@ -457,6 +470,32 @@ __global__ void __launch_bounds__(256) k_syn2_all(const Syn2All a) {
   }
 }
 
+template <int F>
+__global__ void __launch_bounds__(256) k_syn2_one(const Syn2 s, float* __restrict__ out, int tiles_x) {
+  __shared__ float sh[4 * kTS2e + 2 * kT2 * (kKn2 + 1)];
+  syn2_body<F>(s, out, tiles_x, blockIdx.x, blockIdx.y, sh);
+}
+
+// A level runs as one launch per basis when the smallest basis alone has at least two
+// waves of CTAs (four per SM), else as one merged launch over all bases.
+static bool sara_level_per_basis(const int* tiles, int L) {
+  int64_t mn = INT64_MAX;
+  for (int k = 0; k < 8; ++k) mn = std::min<int64_t>(mn, (int64_t)tiles[k] * L);
+  return mn >= 2LL * 4 * num_sms();
+}
+
+#define FHS_F_SWITCH(F, KERNEL, GRID, ...)                               \
+  switch (F) {                                                           \
+    case 2: KERNEL<2><<<GRID, 256, 0, st>>>(__VA_ARGS__); break;         \
+    case 4: KERNEL<4><<<GRID, 256, 0, st>>>(__VA_ARGS__); break;         \
+    case 6: KERNEL<6><<<GRID, 256, 0, st>>>(__VA_ARGS__); break;         \
+    case 8: KERNEL<8><<<GRID, 256, 0, st>>>(__VA_ARGS__); break;         \
+    case 10: KERNEL<10><<<GRID, 256, 0, st>>>(__VA_ARGS__); break;       \
+    case 12: KERNEL<12><<<GRID, 256, 0, st>>>(__VA_ARGS__); break;       \
+    case 14: KERNEL<14><<<GRID, 256, 0, st>>>(__VA_ARGS__); break;       \
+    default: KERNEL<16><<<GRID, 256, 0, st>>>(__VA_ARGS__); break;       \
+  }
+
 struct SynFin2 {
   Syn2 lv[8];          // level-1 description of each basis (ll = its synthesised LL1)
   int64_t dirac_off;
@@ -567,8 +606,17 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
       B.F = 2 * (b + 1);
       t0 += B.tiles_x * ((B.mo1 + kT2 - 1) / kT2);
     }
-    k_ana2_all<<<dim3(t0, L), 256, 0, st>>>(a, coef, S.I);
-    note_launches(1);
+    int tiles[8];
+    for (int k = 0; k < 8; ++k) tiles[k] = (k + 1 < 8 ? a.b[k + 1].tile0 : t0) - a.b[k].tile0;
+    if (sara_level_per_basis(tiles, L)) {
+      for (int k = 0; k < 8; ++k) {
+        FHS_F_SWITCH(a.b[k].F, k_ana2_one, dim3(tiles[k], L), a.b[k], coef, S.I);
+      }
+      note_launches(8);
+    } else {
+      k_ana2_all<<<dim3(t0, L), 256, 0, st>>>(a, coef, S.I);
+      note_launches(1);
+    }
   }
   {
     const int64_t N = (int64_t)cb.n1 * cb.n2;
@@ -610,8 +658,17 @@ void launch_sara_fast(fhs_ctx* ctx, const Cube& cb, const float* x, float* W, co
       a.F[k] = 2 * (b + 1);
       t0 += a.tiles_x[k] * ((s.m1 + kT2 - 1) / kT2);
     }
-    k_syn2_all<<<dim3(t0, L), 256, 0, st>>>(a);
-    note_launches(1);
+    int tiles[8];
+    for (int k = 0; k < 8; ++k) tiles[k] = (k + 1 < 8 ? a.tile0[k + 1] : t0) - a.tile0[k];
+    if (sara_level_per_basis(tiles, L)) {
+      for (int k = 0; k < 8; ++k) {
+        FHS_F_SWITCH(a.F[k], k_syn2_one, dim3(tiles[k], L), a.s[k], a.out[k], a.tiles_x[k]);
+      }
+      note_launches(8);
+    } else {
+      k_syn2_all<<<dim3(t0, L), 256, 0, st>>>(a);
+      note_launches(1);
+    }
   }
   for (int b = 0; b < 8; ++b) {
     Syn2& f = fin.lv[b];
