@@ -8,7 +8,7 @@
 //  * zero rows of the padded image are never read (pruned first column pass),
 //    and the adjoint stores only the rows that survive the crop;
 //  * G: one thread per visibility gathers the 7x7 Kaiser-Bessel taps; weights
-//    from per-tap degree-11 polynomials fitted at context creation;
+//    from per-tap degree-9 polynomials fitted at context creation;
 //  * G^T: one CTA per 64x64 grid tile accumulates in shared memory the
 //    visibilities whose footprint touches the tile (its own sorted bin plus the
 //    crossing classes of its 3 upper/left neighbours) and writes every grid
