@@ -8,12 +8,15 @@ Runs only the FP64 oracle (``oracle/``) on the seeded synthetic inputs of
   (Algorithm 1, Eqs. 9-10), 200 more iterations.
 * ``faceted_pdfb200.json``: 256 x 256, L = 20, 4 x 4 facets, 10 % sine overlap,
   M = 0.5 N in 2 blocks, iSNR 40 dB; 200 PDFB iterations with unit weights.
+* ``precision_small_pdfb100.json``: the precision form's sky, channels and noise (L = 32,
+  Gaussian and point sources with 1 % spectral curvature, M = N in 4 blocks, iSNR 30 dB)
+  on 256 x 256 with 4 x 4 facets; 100 PDFB iterations with unit weights.
 
 Each file holds the parameters the oracle computed (sigma, eps, eta, mu, mu_bar), so the
 GPU side uses exactly the oracle's values, and the results: per-channel SNR
 (Section 4.2), xi and ||r|| of the last iteration, and X at seeded sampled pixels.
 
-Usage: python tests/golden/make_pdfb_runs.py [tiny|faceted ...]
+Usage: python tests/golden/make_pdfb_runs.py [tiny|faceted|precision_small ...]
 """
 from __future__ import annotations
 
@@ -36,6 +39,8 @@ RUNS = {
                  file="tiny_pdfb_schedule.json"),
     "faceted": dict(workload="faceted", over={}, power_iters=60, schedule=[200],
                     file="faceted_pdfb200.json"),
+    "precision_small": dict(workload="precision", over={"n": 256, "Q": 4, "n_blobs": 60, "n_points": 60},
+                            power_iters=40, schedule=[100], file="precision_small_pdfb100.json"),
 }
 N_SAMPLES = 128          # sampled pixels per channel
 

@@ -4,7 +4,10 @@ tests/golden/make_pdfb_runs.py, which runs only the oracle):
 * tiny workload (64 x 64, L = 4, Q = 1): 200 PDFB iterations, one weight update
   (Algorithm 1, Eqs. 9-10), 200 more;
 * faceted workload (256 x 256, L = 20, 4 x 4 facets, sine overlap, 2 blocks): 200 PDFB
-  iterations (Algorithm 2).
+  iterations (Algorithm 2);
+* the precision form's sky and channels on 256 x 256 (L = 32, 4 x 4 facets, point sources
+  and 1 % spectral curvature, M = N in 4 blocks, iSNR 30 dB): 100 PDFB iterations (the
+  L = 32 kernels end to end).
 
 Bar: reconstruction SNR (Section 4.2) of every channel and its mean within 0.05 dB of
 the oracle's, X at the stored sampled pixels within 1e-3 (normwise), the last
@@ -54,7 +57,8 @@ def _context_and_data(rec):
     return spec, inp, Context([cp]), y
 
 
-@pytest.mark.parametrize("fname", ["tiny_pdfb_schedule.json", "faceted_pdfb200.json"])
+@pytest.mark.parametrize("fname", ["tiny_pdfb_schedule.json", "faceted_pdfb200.json",
+                                   "precision_small_pdfb100.json"])
 def test_pdfb_schedule_matches_stored_oracle_run(fname):
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
